@@ -27,7 +27,8 @@
  *      descending, index ascending); s = D[u mod t] with u the node's SplitMix64 draw.
  *  R5  Median split (Alg. 1, Sec. 3 "Median, variances"): order the node's points by the key
  *      (x_s, rk_t(i)) with -0.0 read as +0.0; the left child takes the first h points, where h is
- *      fixed by R1; the split value v is x_s of the first right point (no rounding).
+ *      fixed by R1; the split value v is x_s of the first right point (no rounding), or +inf
+ *      when the right child is empty (possible only with leaf_size 1).
  *  R6  Descent (Alg. 2 "descend", Eq. 1): signed distance d = q_s - v; d < 0 goes left, otherwise
  *      right.  Evaluated as the comparison q_s < v, which has the same sign without rounding.
  *  R7  Search with one leaf per tree (c = T, no priority queue): candidates are the sorted union
@@ -176,8 +177,11 @@ static float split_node(const float *X, int32_t d, int32_t *seq, int64_t cnt, in
         k[i].id = seq[i];
     }
     qsort(k, (size_t)cnt, sizeof(key_t_), key_cmp);
-    float v = k[h].x;
-    key_t_ first_right = k[h];
+    /* With leaf_size 1 the perfect shape can leave the right child empty (h == cnt); the split
+     * value is then +inf, so every point and every finite query goes left. */
+    key_t_ first_right = {INFINITY, 0, -1};
+    if (h < cnt) first_right = k[h];
+    float v = first_right.x;
     /* a point goes left iff its key is below the key of the first right point */
     int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * (size_t)cnt);
     int64_t nl = 0, nr = 0;

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import synth
+from parity import check_forest as _check_forest
 
 
 # ------------------------------------------------------------------ random numbers
@@ -143,52 +144,6 @@ def test_hand_built_forest(golden_dir):
 
 # ------------------------------------------------------------------ forest invariants
 
-def _node_points(F, tree, l, a):
-    lo, hi = (a * F.n) >> l, ((a + 1) * F.n) >> l
-    return F.perm[tree, lo:hi]
-
-
-def _check_forest(F, X, t, seed, shuffle, var_scope, check_dims=True):
-    n, L = F.n, F.L
-    Xd = X.astype(np.float64)
-    gvar = Xd.var(0, ddof=1) if n > 1 else np.zeros(X.shape[1])
-    for tree in range(F.T):
-        assert np.array_equal(np.sort(F.perm[tree]), np.arange(n))        # partition of all points
-        rk = np.array([oracle.rank(seed, tree, shuffle, i) for i in range(n)], dtype=np.uint64)
-        for b in range(1 << L):
-            lo, hi = F.leaf_range(b)
-            assert 1 <= hi - lo <= F.leaf_size
-            assert np.all(np.diff(F.perm[tree, lo:hi]) > 0)                # ascending ids (R2)
-        for l in range(L):
-            for a in range(1 << l):
-                j = (1 << l) - 1 + a
-                pts = _node_points(F, tree, l, a)
-                s, v = int(F.split_dim[tree, j]), float(F.split_val[tree, j])
-                # split dimension among the top-t by numpy's two-pass variance (tolerant to near-ties)
-                var = Xd[pts].var(0, ddof=1) if var_scope == 0 else gvar
-                if var_scope == 0 and len(pts) < 2:
-                    var = np.zeros_like(var)
-                order = np.lexsort((np.arange(len(var)), -var))
-                D = order[:t]
-                if check_dims:
-                    thr = var[D[-1]]
-                    assert var[s] >= thr * (1 - 1e-9)
-                    if var[order[t - 1]] > var[order[t]] * (1 + 1e-9) and \
-                            all(var[D[i]] > var[D[i + 1]] * (1 + 1e-9) for i in range(t - 1)):
-                        assert s == D[oracle.node_draw(seed, tree, j) % t]
-                # median split by the key (x_s, rk), h fixed by the perfect shape (R1, R5)
-                xs = X[pts, s].astype(np.float32) + np.float32(0.0)
-                key_order = np.lexsort((rk[pts], xs))
-                lo = (a * n) >> l
-                h = ((2 * a + 1) * n >> (l + 1)) - lo
-                left_ref = np.sort(pts[key_order[:h]])
-                assert v == xs[key_order[h]]
-                left = _node_points(F, tree, l + 1, 2 * a)
-                assert np.array_equal(np.sort(left), left_ref)
-                right = _node_points(F, tree, l + 1, 2 * a + 1)
-                assert np.all(X[left, s] <= v) and np.all(X[right, s] >= v)
-
-
 @pytest.mark.parametrize("var_scope", [0, 1])
 def test_forest_invariants_mixture(var_scope):
     X, _ = synth.mixture(600, 16, 1, "A", seed=2)
@@ -205,6 +160,19 @@ def test_forest_invariants_quantized_ties():
     F0 = oracle.build_forest(X, 2, 16, t=3, shuffle=0, seed=5)
     _check_forest(F0, X, 3, 5, 0, 0, check_dims=False)
     assert not np.array_equal(F0.perm, F1.perm)
+
+
+@pytest.mark.parametrize("n", [5, 13, 64])
+def test_single_point_leaves(n):
+    # p = 1 (Table 4's smallest leaf): perfect trees may leave a leaf empty, never misplace a point
+    X, Q = synth.mixture(n, 4, 6, "A", seed=n)
+    F = oracle.build_forest(X, 2, 1, t=2, seed=3)
+    _check_forest(F, X, 2, 3, 1, 0)
+    leaf = oracle.descend(F, X)
+    for tr in range(F.T):
+        for i in range(n):
+            lo, hi = F.leaf_range(int(leaf[i, tr]))
+            assert i in F.perm[tr, lo:hi].tolist()
 
 
 def test_trees_are_independent_of_forest_size():
