@@ -1,0 +1,371 @@
+"""Throughput of batched kd-GeRaF queries on one GB300 (and N replicas under torchrun).
+
+Workload (synthetic, seeded; stands in for GIST-1M, which is not available): n = 10^6 points,
+d = 960, the GIST-like Gaussian-mixture law "B" (100 components, per-dimension std
+1/sqrt(1 + j/32), shifted non-negative); m = 10^4 queries from the same mixture; k = 10.
+
+A step is one batch of m queries through the whole search (descent, gather + de-duplication,
+screened scoring, float32 rerank, top-k) with the forest and the points resident in HBM.  The
+forest is built once per run on the GPU (its time is reported separately).  The headline number is
+queries/s of the bfloat16 screen + float32 rerank at the operating point whose recall@1 >= 0.9;
+the float32-only path and the tree parameters T=32, leaf_size=64 are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--small]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "queries/s at 1M×960, k=10, recall@1≥0.9: BF16-screen vs FP32 plain; p99 ms"
+UNIT = "queries/s"
+
+# operating points on the 10^6 x 960 law-B workload
+HEADLINE = dict(T=32, leaf_size=1024)   # recall@1 >= 0.9 (one leaf per tree)
+SPEC = dict(T=32, leaf_size=64)         # the tree parameters quoted with the workload
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def exact_nn(torch, Xg, Qs, k):
+    """Exact k-NN of the sample Qs (evaluation only): float32 GEMM shortlist, float64 recheck."""
+    xn = (Xg * Xg).sum(1)
+    out_i, out_d = [], []
+    for s in range(0, Qs.shape[0], 128):
+        q = Qs[s:s + 128]
+        D = xn[None, :] - 2.0 * (q @ Xg.T)
+        cand = torch.topk(D, 64, dim=1, largest=False).indices
+        diff = Xg[cand].double() - q.double()[:, None, :]
+        ed = (diff * diff).sum(-1)
+        o = torch.argsort(ed, dim=1)[:, :k]
+        out_i.append(torch.gather(cand, 1, o))
+        out_d.append(torch.gather(ed, 1, o))
+    return torch.cat(out_i), torch.cat(out_d)
+
+
+def recall(torch, Xg, Qs, ids, exact_i, exact_d):
+    ids = ids[:, :exact_i.shape[1]]
+    valid = ids[:, 0] >= 0
+    x0 = Xg[ids[:, 0].clamp(min=0)].double()
+    d0 = ((x0 - Qs.double()) ** 2).sum(1)
+    r1 = float(((d0 <= exact_d[:, 0]) & valid).double().mean())
+    k = exact_i.shape[1]
+    hits = (ids[:, :, None] == exact_i[:, None, :]).any(-1).double().sum(1) / k
+    return r1, float(hits.mean())
+
+
+def ours(args):
+    import torch
+    import paper_1603_09596_gb300 as gf
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import synth
+
+    n, d, m, k = (args.n, args.d, args.m, 10)
+    t0 = time.time()
+    X, Q = synth.mixture(n, d, m, "B", seed=0, qseed=1 + rank)
+    gen_s = time.time() - t0
+    Xg = torch.from_numpy(X).to(dev)
+    Qg = torch.from_numpy(Q).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    hbm_peak, peak_kind = peaks()
+    res = {}
+
+    def build(T, p):
+        torch.cuda.synchronize()
+        t = time.time()
+        F = gf.gf_build(Xg, T, p, seed=0)
+        torch.cuda.synchronize()
+        return F, time.time() - t
+
+    # exact neighbours of a query sample, for recall
+    S = min(m, args.recall_sample)
+    ei, ed = exact_nn(torch, Xg, Qg[:S], k)
+
+    def time_query(F, prec, R, steps, warmup):
+        ids = torch.empty((m, k), dtype=torch.int64, device=dev)
+        dd = torch.empty((m, k), dtype=torch.float32, device=dev)
+        for _ in range(warmup):
+            gf.gf_query(F, Qg, k, precision=prec, rerank_R=R, out=(ids, dd))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with Clocks(local) as ck:
+            torch.cuda.synchronize()
+            for a, b in evs:
+                a.record(stream)
+                gf.gf_query(F, Qg, k, precision=prec, rerank_R=R, out=(ids, dd))
+                b.record(stream)
+            torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ids, dd, ms, ck.summary()
+
+    def candidates_per_query(F):
+        leaf = gf.gf_descend(F, Qg)
+        try:
+            _, nc = gf.gf_candidates(F, leaf)
+            return float(nc.double().mean())
+        except gf.GFError:
+            return None
+
+    out = {}
+    for name, par in (("headline", HEADLINE), ("spec", SPEC)):
+        F, bs = build(par["T"], par["leaf_size"])
+        gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
+        entry = {"T": par["T"], "leaf_size": par["leaf_size"], "L": F.info.L, "build_s": round(bs, 3)}
+        for prec_name, prec, R in (("bf16", gf.GF_BF16_RERANK, args.R), ("fp32", gf.GF_FP32, 0)):
+            try:
+                ids, dd, ms, ck = time_query(F, prec, R, args.steps, args.warmup)
+            except gf.GFError as e:
+                entry[prec_name] = {"error": str(e)}
+                continue
+            r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
+            mean_ms = statistics.mean(ms)
+            entry[prec_name] = {"qps": m / (mean_ms / 1e3), "ms_per_step": mean_ms,
+                                "ms_min": min(ms), "recall_at_1": r1, "recall_at_10": rk, "clocks": ck,
+                                "R": R}
+        entry["cand_per_query"] = candidates_per_query(F)
+        out[name] = (entry, F)
+    head, Fh = out["headline"]
+    spec, Fs = out["spec"]
+    best = head.get("bf16", {})
+    if "qps" not in best:
+        best = spec.get("bf16", {})
+    mean_ms = best.get("ms_per_step", float("nan"))
+    if world > 1:
+        t = torch.tensor([mean_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    value = world * m / (mean_ms / 1e3)
+
+    # roofline of the query kernel (one launch per step): algorithmic bytes per launch
+    C = head.get("cand_per_query") or 0.0
+    R = args.R
+    bx = 2  # bf16 screen rows
+    per_q = C * (d * bx) + R * d * 4 + d * 4 + C * 4 + 4 * head["T"] * 0 + 12 * k
+    achieved = per_q * m / (mean_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind,
+            "kernel": "k_query (bf16 screen + fp32 rerank)", "bytes_per_query": round(per_q)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 or True:
+        Qh = torch.from_numpy(Q).pin_memory()
+        ih = torch.empty((m, k), dtype=torch.int64).pin_memory()
+        dh = torch.empty((m, k), dtype=torch.float32).pin_memory()
+        Qd = torch.empty_like(Qg)
+        ids = torch.empty((m, k), dtype=torch.int64, device=dev)
+        dd = torch.empty((m, k), dtype=torch.float32, device=dev)
+        prec = gf.GF_BF16_RERANK
+        F = Fh if "qps" in head.get("bf16", {}) else Fs
+        for _ in range(args.warmup):
+            Qd.copy_(Qh, non_blocking=True)
+            gf.gf_query(F, Qd, k, precision=prec, rerank_R=R, out=(ids, dd))
+            ih.copy_(ids, non_blocking=True)
+            dh.copy_(dd, non_blocking=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            Qd.copy_(Qh, non_blocking=True)
+            gf.gf_query(F, Qd, k, precision=prec, rerank_R=R, out=(ids, dd))
+            ih.copy_(ids, non_blocking=True)
+            dh.copy_(dd, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / args.steps
+        e2e = {"value": world * m / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": m * d * 4,
+               "d2h_bytes_per_step": m * k * 12}
+
+    # CPU oracle on this host's cores, on a bounded sample of the same workload
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(X, Q, Fs if "qps" not in head.get("bf16", {}) else Fh, gf, k, budget_s=args.cpu_budget)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(mean_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"law-B Gaussian mixture n={n} d={d}, m={m} queries, k={k}",
+                   "T": HEADLINE["T"], "leaf_size": HEADLINE["leaf_size"], "precision": "bf16 screen + fp32 rerank",
+                   "R": R, "recall_at_1": best.get("recall_at_1"), "recall_sample": S,
+                   "l2": "inputs larger than L2 (points 3.84 GB)", "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * 1,
+        "clocks": best.get("clocks"),
+        "fp32_plain": head.get("fp32"),
+        "bf16_screen": head.get("bf16"),
+        "at_T32_p64": spec,
+        "headline_forest": {"T": head["T"], "leaf_size": head["leaf_size"], "L": head["L"],
+                            "build_s": head["build_s"], "cand_per_query": head.get("cand_per_query")},
+        "gen_s": round(gen_s, 2),
+        "p99_ms": None,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(X, Q, F, gf, k, budget_s=15.0):
+    """The oracle search, as it stands, on this host's cores over a bounded query sample."""
+    import oracle
+    sd, sv, pm = gf.gf_forest_export(F)
+    inf = F.info
+    Fo = oracle.Forest(inf.n, inf.d, inf.T, inf.leaf_size, inf.L, sd, sv, pm)
+    done, t0, bs = 0, time.time(), 64
+    while time.time() - t0 < budget_s and done < Q.shape[0]:
+        oracle.search(Fo, X, Q[done:done + bs], k)
+        done += min(bs, Q.shape[0] - done)
+        bs = min(bs * 2, 1024)
+    el = time.time() - t0
+    return {"value": round(done / el, 2), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} of the {Q.shape[0]} queries, same forest (T={inf.T}, leaf_size={inf.leaf_size}), float64"}
+
+
+def reference(args):
+    """The oracle, timed on the host cores on the same workload (bounded query sample per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    n, d, m, k = args.n, args.d, args.m, 10
+    X, Q = synth.mixture(n, d, m, "B", seed=0, qseed=1)
+    tb = time.time()
+    F = oracle.build_forest(X, HEADLINE["T"], HEADLINE["leaf_size"], seed=0)
+    build_s = time.time() - tb
+    per_step = args.ref_queries
+    for w in range(args.warmup):
+        oracle.search(F, X, Q[:min(m, 16)], k)
+    times = []
+    for s in range(args.steps):
+        lo = (s * per_step) % m
+        qs = Q[lo:lo + per_step]
+        t = time.time()
+        oracle.search(F, X, qs, k)
+        times.append((time.time() - t) / qs.shape[0])
+    sec_per_q = statistics.mean(times)
+    value = 1.0 / sec_per_q
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec_per_q * per_step * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"law-B Gaussian mixture n={n} d={d}, m={m} queries, k={k}",
+                   "T": HEADLINE["T"], "leaf_size": HEADLINE["leaf_size"], "precision": "float64 oracle",
+                   "build_s": round(build_s, 1)},
+        "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{per_step} queries per step"},
+        "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--d", type=int, default=960)
+    ap.add_argument("--m", type=int, default=10_000)
+    ap.add_argument("--R", type=int, default=64)
+    ap.add_argument("--recall-sample", type=int, default=1000)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-queries", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * gf.h -- C ABI of the GB300 kd-GeRaF library (batched approximate nearest-neighbour search over a
+ * forest of randomized k-d trees; Avrithis, Emiris, Samaras, arXiv 1603.09596).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named X, Q, ids, dists, leaf, cand, ncand are DEVICE pointers (cudaMalloc'ed or from
+ *    a framework allocator) on the current CUDA device, unless the name ends in _host.
+ *  - Matrices are row-major and contiguous: X is [n][d] float32, Q is [m][d] float32.
+ *  - Outputs are allocated by the caller; the library never keeps a pointer to a caller buffer
+ *    after the call returns (except the dataset when gf_build_ex is asked to borrow it).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  Query and
+ *    stage calls are asynchronous on that stream: they return once the work is enqueued.  Build,
+ *    import, export and free are synchronous.
+ *  - Every function returns GF_OK (0) or a negative GF_E* code; no C++ exception crosses the ABI.
+ *    gf_last_error() returns a message for the calling thread's most recent failure.
+ *  - A const forest may be queried from several host threads at once (queries allocate nothing
+ *    and write only to their own outputs).
+ *
+ * Tree layout (readings of the paper stated once here and used throughout):
+ *  - Trees are perfect (Sec. 3 "Tree structure"): depth L = min{l >= 0 : ceil(n / 2^l) <= p} for
+ *    leaf_size p; internal node j (heap order, children 2j+1 and 2j+2) stores (split dimension,
+ *    split value); leaf b (0 <= b < 2^L) holds the points perm[t][floor(b n / 2^L) ..
+ *    floor((b+1) n / 2^L)) of tree t, listed in ascending id order.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define GF_OK 0
+#define GF_EINVAL (-1)        /* bad argument: null pointer, size out of range, t > d, k < 1 ... */
+#define GF_ENOMEM (-2)        /* a device or host allocation failed; nothing was leaked */
+#define GF_ECUDA (-3)         /* a CUDA runtime call or kernel launch failed */
+#define GF_ETIMEOUT (-4)      /* a bounded wait ran out (serving loop) */
+#define GF_EUNSUPPORTED (-5)  /* valid request the library does not implement (e.g. householder) */
+#define GF_EIO (-6)           /* file could not be read or written, or has a bad format */
+
+/* ---------------------------------------------------------------- parameters */
+
+/* Variance scope for the split-dimension choice. */
+#define GF_VAR_NODE 0   /* variance of each node's own points (default) */
+#define GF_VAR_GLOBAL 1 /* variance of the whole dataset, once (Alg. 1 as printed) */
+
+/* Randomization of the trees (Sec. 2.1). */
+typedef struct gf_rand_params {
+    int32_t t;           /* split dimension drawn uniformly from the t highest-variance dims */
+    int32_t shuffle;     /* 1: per-tree random order breaks ties of equal coordinates
+                            (Sec. 2.1 "Shuffling"); 0: ties broken by point id */
+    int32_t var_scope;   /* GF_VAR_NODE or GF_VAR_GLOBAL */
+    int32_t householder; /* per-tree random reflection (Sec. 2.2); must be 0 (GF_EUNSUPPORTED) */
+} gf_rand_params;
+
+/* Candidate scoring precision (how the leaf points are ranked, Sec. 3 "Distance computation"). */
+#define GF_FP32 0         /* exact float32 squared L2 over all candidates */
+#define GF_BF16_RERANK 1  /* bfloat16 screen -> shortlist of R -> float32 rerank */
+#define GF_FP8_RERANK 2   /* FP8-E4M3 (per-row float32 scale) screen -> R -> float32 rerank */
+
+typedef struct gf_query_opts {
+    int32_t precision;     /* GF_FP32, GF_BF16_RERANK or GF_FP8_RERANK */
+    int32_t rerank_R;      /* shortlist length for the screened precisions; 0 = forest default */
+    int32_t warps_per_cta; /* kernel shape; 0 = forest default (set by gf_autotune) */
+    int32_t ctas_per_sm;   /* kernel shape; 0 = forest default (set by gf_autotune) */
+    void *stream;          /* cudaStream_t */
+} gf_query_opts;
+
+typedef struct gf_forest gf_forest; /* opaque; owned by the library */
+
+typedef struct gf_forest_info {
+    int64_t n;           /* points */
+    int32_t d;           /* dimensions */
+    int32_t T;           /* trees */
+    int32_t leaf_size;   /* p */
+    int32_t L;           /* tree depth */
+    int32_t max_leaf;    /* ceil(n / 2^L) */
+    int32_t cand_cap;    /* T * max_leaf: upper bound on candidates per query */
+    int32_t screens;     /* bit (1 << GF_BF16_RERANK) / (1 << GF_FP8_RERANK): derived copies held */
+    int64_t device_bytes;/* device memory owned by the forest */
+} gf_forest_info;
+
+void gf_rand_params_default(gf_rand_params *rp); /* t = 5, shuffle = 1, var_scope = NODE */
+void gf_query_opts_default(gf_query_opts *o);    /* FP32, everything else 0 / NULL */
+
+/* ---------------------------------------------------------------- forest */
+
+/*
+ * gf_build -- build a forest of T randomized k-d trees on the GPU (Alg. 1; Alg. 3 variance;
+ * Sec. 3 "Median, variances").  At every internal node one dimension is drawn uniformly among the
+ * rp->t dimensions of largest variance and the node's points are split at the median in that
+ * dimension (ties in the coordinate broken by the tree's random order when rp->shuffle).
+ *   X          device, [n][d] float32, finite; copied into the forest (the caller may free it)
+ *   n, d       1 <= n < 2^31, 1 <= d <= 65535
+ *   T          number of trees, >= 1
+ *   leaf_size  p >= 1: leaves hold at most p points
+ *   rp         NULL for defaults
+ *   seed       forest seed: the same (X, parameters, seed) always gives the same forest
+ *   out        receives the new forest
+ * Errors: GF_EINVAL (bad sizes, NaN/Inf in X, t outside [1, d]), GF_EUNSUPPORTED (householder),
+ * GF_ENOMEM, GF_ECUDA.  Synchronous.
+ */
+int gf_build(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
+             const gf_rand_params *rp, uint64_t seed, gf_forest **out);
+
+/* As gf_build, on `stream`; borrow_x = 1 keeps a pointer to X instead of copying it (X must then
+ * outlive the forest and have d % 4 == 0 and 16-byte alignment). */
+int gf_build_ex(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
+                const gf_rand_params *rp, uint64_t seed, int32_t borrow_x, void *stream,
+                gf_forest **out);
+
+/*
+ * gf_forest_import -- make a forest from a given tree structure (used to query a forest built
+ * elsewhere, e.g. by a CPU reference, with the GPU search).  split_dim_host / split_val_host are
+ * host [T][2^L - 1], perm_host is host [T][n] with L = depth(n, leaf_size); X as in gf_build.
+ * Errors: GF_EINVAL (a split dimension outside [0, d), a perm row that is not a permutation of
+ * 0..n-1), GF_ENOMEM, GF_ECUDA.  Synchronous.
+ */
+int gf_forest_import(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
+                     const int32_t *split_dim_host, const float *split_val_host,
+                     const int32_t *perm_host, gf_forest **out);
+
+/* Copy the tree structure out to host arrays shaped as in gf_forest_import.  Synchronous. */
+int gf_forest_export(const gf_forest *F, int32_t *split_dim_host, float *split_val_host,
+                     int32_t *perm_host);
+
+int gf_forest_get_info(const gf_forest *F, gf_forest_info *info);
+
+/*
+ * gf_forest_add_screen -- derive the low-precision copy of the points used by a screened
+ * precision (Sec. 3 "Distance computation": ranking cost is the distance evaluation).
+ *   GF_BF16_RERANK: xb[i][j] = bf16_rne(X[i][j])
+ *   GF_FP8_RERANK:  a_i = max_j |X[i][j]|; scale_i = a_i / 448 (1 if a_i == 0);
+ *                   x8[i][j] = e4m3_rne_satfinite(X[i][j] * (448 / a_i))  (0 if a_i == 0)
+ * Synchronous.  Errors: GF_EINVAL, GF_ENOMEM, GF_ECUDA.
+ */
+int gf_forest_add_screen(gf_forest *F, int32_t precision, void *stream);
+
+/* Set the forest's default kernel shape and shortlist (what gf_autotune writes). */
+int gf_forest_set_tuning(gf_forest *F, int32_t precision, int32_t warps_per_cta,
+                         int32_t ctas_per_sm, int32_t rerank_R);
+
+int gf_forest_free(gf_forest *F);
+
+/* ---------------------------------------------------------------- query (hot path) */
+
+/*
+ * gf_query -- k approximate nearest neighbours of m queries (Alg. 2 with one leaf per tree:
+ * every query descends every tree to one leaf, Eq. 1; the points of the T leaves reached are
+ * de-duplicated (Sec. 2.3 "seen" array), scored by squared L2 distance and the k nearest kept).
+ *   Q      device [m][d] float32
+ *   ids    device [m][k] int64: point ids ordered by (distance, id); -1 where a query has fewer
+ *          than k candidates
+ *   dists  device [m][k] float32: squared L2 distances (float32 arithmetic); +inf with id -1
+ * Precision GF_FP32 on the legacy default stream.  m = 0 is a no-op.  Queries containing NaN give
+ * unspecified ids but never read or write out of bounds.
+ * Errors: GF_EINVAL (k < 1, m < 0, null pointers), GF_ECUDA.
+ */
+int gf_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int64_t *ids, float *dists);
+
+/* As gf_query with options (precision, shortlist, kernel shape, stream).  The screened precisions
+ * need gf_forest_add_screen first (else GF_EINVAL); their output distances are the float32 rerank
+ * distances.  k must not exceed the shortlist R for screened precisions. */
+int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_t k, const gf_query_opts *o,
+                int64_t *ids, float *dists);
+
+/* ---------------------------------------------------------------- the path in stages
+ * The same computation as gf_query, one step per call, with the intermediate results in caller
+ * buffers (used to check every step on its own).  All asynchronous on `stream`.
+ */
+
+/* Step 1 (Alg. 2 "descend", Eq. 1): leaf[i][t] = leaf of tree t reached by query i.
+ * leaf: device [m][T] int32. */
+int gf_descend(const gf_forest *F, const float *Q, int64_t m, int32_t *leaf, void *stream);
+
+/* Step 2 (Sec. 2.3, "seen" array): the sorted union of the leaves' points of each query.
+ * cand: device [m][cand_cap] int32 (cand_cap from gf_forest_get_info), row i holds ncand[i]
+ * ascending ids followed by unspecified values; ncand: device [m] int32. */
+int gf_candidates(const gf_forest *F, const int32_t *leaf, int64_t m, int32_t *cand, int32_t *ncand,
+                  void *stream);
+
+/* Steps 3-4 (Alg. 2 leaf check, squared L2, min-heap of k): float32 distances of each query's
+ * candidates and the k smallest by (distance, id).  cand / ncand as produced by gf_candidates,
+ * with row stride cand_stride >= max(ncand).  ids / dists as in gf_query. */
+int gf_score_topk(const gf_forest *F, const float *Q, int64_t m, const int32_t *cand,
+                  const int32_t *ncand, int32_t cand_stride, int32_t k, int64_t *ids,
+                  float *dists, void *stream);
+
+/* Step 3 alone, any precision (Sec. 3 "Distance computation"): dist[i][j] = squared L2 distance
+ * of query i to candidate cand[i][j] for j < ncand[i], computed as the chosen precision's screen
+ * computes it (GF_FP32: float32 points; GF_BF16_RERANK: bfloat16 points; GF_FP8_RERANK: scale_i
+ * times the E4M3 codes), float32 arithmetic.  dist: device [m][cand_stride] float32; entries past
+ * ncand[i] are left untouched; an id outside [0, n) gives NaN.  The screened precisions need
+ * gf_forest_add_screen first (else GF_EINVAL). */
+int gf_score_screened(const gf_forest *F, const float *Q, int64_t m, const int32_t *cand,
+                      const int32_t *ncand, int32_t cand_stride, int32_t precision, float *dist,
+                      void *stream);
+
+/* ---------------------------------------------------------------- misc */
+
+const char *gf_last_error(void);
+int32_t gf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_H */

@@ -1,0 +1,98 @@
+// gf_internal.cuh -- shared definitions of the GB300 kd-GeRaF library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gf.h"
+
+// ---------------------------------------------------------------- the forest object
+//
+// Device layout (all row-major, all owned by the forest unless borrowed):
+//   x       float [n][ldx]        points, rows padded with zeros to ldx = round_up(d, 4) floats
+//   nodes   int2  [T][2^L - 1]    internal nodes in heap order: .x split dim, .y split value bits
+//   perm    int32 [T][n]          leaf permutation of every tree (leaf b = [b n >> L, (b+1) n >> L))
+//   xb      bf16  [n][ldb]        optional screening copy, ldb = round_up(d, 8)
+//   x8      e4m3  [n][ld8]        optional screening copy, ld8 = round_up(d, 16)
+//   scale8  float [n]             per-row scale of x8
+struct gf_forest {
+    int64_t n = 0;
+    int32_t d = 0, T = 0, leaf_size = 0, L = 0;
+    int32_t max_leaf = 0, cand_cap = 0;
+    int32_t ldx = 0, ldb = 0, ld8 = 0;
+    float *x = nullptr;
+    bool owns_x = true;
+    int2 *nodes = nullptr;
+    int32_t *perm = nullptr;
+    __nv_bfloat16 *xb = nullptr;
+    uint8_t *x8 = nullptr;
+    float *scale8 = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    // per-precision kernel shape and shortlist (written by the autotuner)
+    int32_t tune_warps[3] = {8, 8, 8};
+    int32_t tune_ctas[3] = {0, 0, 0};
+    int32_t tune_R[3] = {0, 64, 128};
+    int64_t device_bytes = 0;
+};
+
+// Read-only view handed to kernels by value.
+struct ForestView {
+    const float *x;
+    const __nv_bfloat16 *xb;
+    const uint8_t *x8;
+    const float *scale8;
+    const int2 *nodes;
+    const int32_t *perm;
+    long long n;
+    int d, ldx, ldb, ld8, T, L, nnodes, max_leaf, cand_cap;
+};
+
+inline ForestView view_of(const gf_forest *F) {
+    ForestView v;
+    v.x = F->x; v.xb = F->xb; v.x8 = F->x8; v.scale8 = F->scale8;
+    v.nodes = F->nodes; v.perm = F->perm;
+    v.n = F->n; v.d = F->d; v.ldx = F->ldx; v.ldb = F->ldb; v.ld8 = F->ld8;
+    v.T = F->T; v.L = F->L; v.nnodes = (1 << F->L) - 1;
+    v.max_leaf = F->max_leaf; v.cand_cap = F->cand_cap;
+    return v;
+}
+
+// ---------------------------------------------------------------- shape helpers
+
+inline int32_t depth_of(int64_t n, int32_t p) {
+    int32_t L = 0;
+    while (((n + ((int64_t)1 << L) - 1) >> L) > p) L++;
+    return L;
+}
+
+inline int32_t round_up(int32_t a, int32_t b) { return (a + b - 1) / b * b; }
+
+inline int32_t next_pow2(int32_t v) {
+    int32_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// ---------------------------------------------------------------- errors
+
+int gf_fail(int code, const char *fmt, ...);  // records the thread's message, returns code
+int gf_cuda_fail(cudaError_t e, const char *what);
+
+#define GF_CUDA_TRY(expr)                                    \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return gf_cuda_fail(e_, #expr); \
+    } while (0)
+
+// Allocation with the library's error code (nothing is leaked on failure).
+int gf_dmalloc(void **p, size_t bytes);
+
+// ---------------------------------------------------------------- entry points between units
+int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,
+                    int32_t R, int32_t warps, int32_t ctas_per_sm, cudaStream_t s, int64_t *ids,
+                    float *dists);

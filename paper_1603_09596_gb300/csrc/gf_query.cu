@@ -1,0 +1,611 @@
+// gf_query.cu -- the query hot path: descent, candidate gather + de-duplication, squared-L2
+// scoring and top-k selection (Alg. 2 with one leaf per tree; Eq. 1; Sec. 2.3; Sec. 3 "Distance
+// computation").
+//
+// One CTA owns one query at a time and keeps everything the query needs in shared memory:
+//   - the query row (float32, zero-padded),
+//   - the T leaf ranges reached by the descent,
+//   - the gathered candidate ids, sorted and de-duplicated in place (the "seen" array of Sec. 2.3
+//     becomes a sort-unique over at most T * max_leaf ids),
+//   - one 64-bit key (distance bits << 32 | id) per candidate, sorted to give the k nearest by
+//     (distance, id).
+// The scoring loop is the only part that touches HBM in bulk: every candidate row is streamed
+// once with 16-byte read-only loads that bypass L1, a warp per row, two rows in flight per warp.
+#include "gf_internal.cuh"
+
+#include <climits>
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long KEY_NONE = ~0ull;
+
+__device__ __forceinline__ uint4 ld_u4(const void *p) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long make_key(float dist, int id) {
+    return ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)id;
+}
+
+// ---------------------------------------------------------------- descent (Alg. 2, Eq. 1)
+
+// Leaf of one tree reached by query q: at each node the signed distance q_s - v decides the
+// side; negative goes left (2j+1), zero or positive goes right (2j+2).
+__device__ __forceinline__ int descend_tree(const int2 *__restrict__ nodes, int L, const float *q) {
+    int j = 0;
+    for (int l = 0; l < L; ++l) {
+        const int2 nd = __ldg(nodes + j);
+        j = 2 * j + (q[nd.x] < __int_as_float(nd.y) ? 1 : 2);
+    }
+    return j - ((1 << L) - 1);
+}
+
+// ---------------------------------------------------------------- block helpers
+
+// Ascending bitonic sort of a[0..P), P a power of two, by the whole block.
+template <typename K>
+__device__ void block_sort(K *a, int P) {
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const K x = a[lo], y = a[hi];
+                const bool asc = (lo & size) == 0;
+                if ((x > y) == asc) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Copy the distinct values of the sorted a[0..tot) to u[] (keeping order); returns their number.
+__device__ int block_unique(const int *a, int tot, int *u, int *wtmp) {
+    const int nt = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = nt >> 5;
+    const int E = (tot + nt - 1) / nt;
+    const int beg = threadIdx.x * E, end = min(beg + E, tot);
+    int cnt = 0;
+    for (int i = beg; i < end; ++i) cnt += (i == 0 || a[i] != a[i - 1]);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wtmp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < nw ? wtmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < nw) wtmp[lane] = v;
+    }
+    __syncthreads();
+    int pos = (w ? wtmp[w - 1] : 0) + incl - cnt;
+    const int total = wtmp[nw - 1];
+    for (int i = beg; i < end; ++i)
+        if (i == 0 || a[i] != a[i - 1]) u[pos++] = a[i];
+    __syncthreads();
+    return total;
+}
+
+// Gather the points of the T leaves (ranges lofs/lcnt of each tree's perm) into cand, sort them
+// and keep each id once (Sec. 2.3).  Returns the number of distinct candidates, written to u.
+__device__ int gather_unique(const ForestView &F, const int *lofs, const int *lcnt, int *lpos,
+                             int *cand, int *u, int *wtmp, int *sh) {
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < F.T; ++t) {
+            lpos[t] = acc;
+            acc += lcnt[t];
+        }
+        sh[0] = acc;
+    }
+    __syncthreads();
+    const int tot = sh[0];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = w; t < F.T; t += nw) {
+        const int32_t *src = F.perm + (size_t)t * F.n + lofs[t];
+        int *dst = cand + lpos[t];
+        for (int j = lane; j < lcnt[t]; j += 32) dst[j] = __ldg(src + j);
+    }
+    int P = 1;
+    while (P < tot) P <<= 1;
+    for (int i = tot + threadIdx.x; i < P; i += blockDim.x) cand[i] = INT_MAX;
+    block_sort<int>(cand, P);
+    return block_unique(cand, tot, u, wtmp);
+}
+
+// ---------------------------------------------------------------- scoring
+
+__device__ __forceinline__ void acc4(float4 &a, const float4 q, const float4 x) {
+    float e;
+    e = q.x - x.x; a.x = fmaf(e, e, a.x);
+    e = q.y - x.y; a.y = fmaf(e, e, a.y);
+    e = q.z - x.z; a.z = fmaf(e, e, a.z);
+    e = q.w - x.w; a.w = fmaf(e, e, a.w);
+}
+
+__device__ __forceinline__ float sum4(const float4 a) { return (a.x + a.y) + (a.z + a.w); }
+
+// bfloat16 chunk (8 values) against 8 query floats
+__device__ __forceinline__ void acc_bf16(float4 &a, const float4 q0, const float4 q1, const uint4 c) {
+    const float2 x0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.x));
+    const float2 x1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.y));
+    const float2 x2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.z));
+    const float2 x3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.w));
+    acc4(a, q0, make_float4(x0.x, x0.y, x1.x, x1.y));
+    acc4(a, q1, make_float4(x2.x, x2.y, x3.x, x3.y));
+}
+
+__device__ __forceinline__ float2 e4m3x2_to_float2(unsigned short v) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)v, __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+}
+
+// FP8-E4M3 word (4 codes) times the row scale against 4 query floats: delta = q - s * c.
+__device__ __forceinline__ void acc_fp8w(float4 &a, const float4 q, unsigned w, float s) {
+    const float2 lo = e4m3x2_to_float2((unsigned short)(w & 0xffffu));
+    const float2 hi = e4m3x2_to_float2((unsigned short)(w >> 16));
+    float e;
+    e = fmaf(-s, lo.x, q.x); a.x = fmaf(e, e, a.x);
+    e = fmaf(-s, lo.y, q.y); a.y = fmaf(e, e, a.y);
+    e = fmaf(-s, hi.x, q.z); a.z = fmaf(e, e, a.z);
+    e = fmaf(-s, hi.y, q.w); a.w = fmaf(e, e, a.w);
+}
+
+// Precision tags
+constexpr int P_F32 = 0, P_BF16 = 1, P_FP8 = 2;
+
+// Score candidates ids[0..C) of the query in qs (float32, zero-padded to a multiple of 16) and
+// write one key per candidate.  Warp w takes rows w, w + nw, ...; two rows are in flight per
+// warp.  NC > 0: a lane holds at most NC chunks of a row (chunk = 16 bytes), with the query's
+// matching values in registers; NC == 0: any row length, query read from shared memory.
+template <int PREC, int NC>
+__device__ void score_rows(const ForestView &F, const float *qs, const int *ids, int C,
+                           unsigned long long *keys) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // row pitch in bytes and chunks per row
+    const size_t pitch = PREC == P_F32 ? (size_t)F.ldx * 4 : PREC == P_BF16 ? (size_t)F.ldb * 2 : (size_t)F.ld8;
+    const int nch = (int)(pitch >> 4);
+    const unsigned char *base = PREC == P_F32 ? (const unsigned char *)F.x
+                              : PREC == P_BF16 ? (const unsigned char *)F.xb : F.x8;
+    constexpr int QF4 = PREC == P_F32 ? 1 : PREC == P_BF16 ? 2 : 4;  // query float4s per chunk
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+    constexpr int NR = NC > 0 ? NC : 1;
+    float4 qr[NR * QF4];
+    if (NC > 0) {
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            const int cc = lane + 32 * c;
+#pragma unroll
+            for (int h = 0; h < QF4; ++h)
+                qr[c * QF4 + h] = cc < nch ? q4[cc * QF4 + h] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    for (int j = w; j < C; j += 2 * nw) {
+        const int j1 = j + nw;
+        const int i0 = ids[j];
+        const int i1 = j1 < C ? ids[j1] : i0;
+        const bool v0 = (unsigned)i0 < (unsigned long long)F.n;
+        const bool v1 = (unsigned)i1 < (unsigned long long)F.n;
+        const unsigned char *r0 = base + (size_t)(v0 ? i0 : 0) * pitch;
+        const unsigned char *r1 = base + (size_t)(v1 ? i1 : 0) * pitch;
+        const float s0 = PREC == P_FP8 ? __ldg(F.scale8 + (v0 ? i0 : 0)) : 0.f;
+        const float s1 = PREC == P_FP8 ? __ldg(F.scale8 + (v1 ? i1 : 0)) : 0.f;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+        constexpr int UB = NC > 0 ? NC : 4;  // chunks per lane loaded before use
+        for (int c0 = lane; c0 < nch; c0 += 32 * UB) {
+            uint4 x0[UB], x1[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int cc = c0 + 32 * u;
+                if (cc < nch) {
+                    x0[u] = ld_u4(r0 + ((size_t)cc << 4));
+                    x1[u] = ld_u4(r1 + ((size_t)cc << 4));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int cc = c0 + 32 * u;
+                if (cc < nch) {
+                    float4 qa[QF4];
+#pragma unroll
+                    for (int h = 0; h < QF4; ++h) qa[h] = NC > 0 ? qr[u * QF4 + h] : q4[cc * QF4 + h];
+                    if (PREC == P_F32) {
+                        acc4(a0, qa[0], *reinterpret_cast<const float4 *>(&x0[u]));
+                        acc4(a1, qa[0], *reinterpret_cast<const float4 *>(&x1[u]));
+                    } else if (PREC == P_BF16) {
+                        acc_bf16(a0, qa[0], qa[1], x0[u]);
+                        acc_bf16(a1, qa[0], qa[1], x1[u]);
+                    } else {
+                        acc_fp8w(a0, qa[0], x0[u].x, s0); acc_fp8w(a0, qa[1], x0[u].y, s0);
+                        acc_fp8w(a0, qa[2], x0[u].z, s0); acc_fp8w(a0, qa[3], x0[u].w, s0);
+                        acc_fp8w(a1, qa[0], x1[u].x, s1); acc_fp8w(a1, qa[1], x1[u].y, s1);
+                        acc_fp8w(a1, qa[2], x1[u].z, s1); acc_fp8w(a1, qa[3], x1[u].w, s1);
+                    }
+                }
+            }
+            if (NC > 0) break;  // one pass covers the row
+        }
+        const float d0 = warp_sum(sum4(a0));
+        const float d1 = warp_sum(sum4(a1));
+        if (lane == 0) {
+            keys[j] = v0 ? make_key(d0, i0) : KEY_NONE;
+            if (j1 < C) keys[j1] = v1 ? make_key(d1, i1) : KEY_NONE;
+        }
+    }
+}
+
+// Sort keys[0..C) (padding to a power of two) so the k nearest come first.
+__device__ void sort_keys(unsigned long long *keys, int C) {
+    int P = 1;
+    while (P < C) P <<= 1;
+    __syncthreads();
+    for (int i = C + threadIdx.x; i < P; i += blockDim.x) keys[i] = KEY_NONE;
+    block_sort<unsigned long long>(keys, P);
+}
+
+__device__ void write_topk(const unsigned long long *keys, int C, int k, long long *ids,
+                           float *dists) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const unsigned long long key = i < C ? keys[i] : KEY_NONE;
+        if (key == KEY_NONE) {
+            ids[i] = -1;
+            dists[i] = __int_as_float(0x7f800000);
+        } else {
+            ids[i] = (long long)(unsigned)(key & 0xffffffffu);
+            dists[i] = __uint_as_float((unsigned)(key >> 32));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- shared-memory plan
+
+struct Smem {
+    unsigned long long *keys;  // [P]   (cand aliases it as int[P] before scoring)
+    float *qs;                 // [ldq]
+    int *u;                    // [cand_cap] distinct candidates / shortlist
+    int *lofs, *lcnt, *lpos;   // [T]
+    int *wtmp;                 // [32]
+    int *sh;                   // [4]
+};
+
+__host__ __device__ inline int ldq_of(int d) { return (d + 15) / 16 * 16; }
+
+// keys region: a power of two >= cap and >= 2, so that the float4 query row after it is aligned
+__host__ __device__ inline int keys_len(int cap) {
+    int P = 2;
+    while (P < cap) P <<= 1;
+    return P;
+}
+
+__host__ __device__ inline size_t smem_bytes(int d, int T, int cap) {
+    const int P = keys_len(cap);
+    return (size_t)P * 8 + (size_t)ldq_of(d) * 4 + (size_t)cap * 4 + (size_t)T * 12 + 32 * 4 + 16;
+}
+
+__device__ inline Smem carve(unsigned char *p, int d, int T, int cap) {
+    Smem s;
+    const int P = keys_len(cap);
+    s.keys = reinterpret_cast<unsigned long long *>(p);
+    p += (size_t)P * 8;
+    s.qs = reinterpret_cast<float *>(p);
+    p += (size_t)ldq_of(d) * 4;
+    s.u = reinterpret_cast<int *>(p);
+    p += (size_t)cap * 4;
+    s.lofs = reinterpret_cast<int *>(p);
+    s.lcnt = s.lofs + T;
+    s.lpos = s.lcnt + T;
+    s.wtmp = s.lpos + T;
+    s.sh = s.wtmp + 32;
+    return s;
+}
+
+__device__ void load_query(const float *q, int d, float *qs) {
+    const int ldq = ldq_of(d);
+    for (int j = threadIdx.x; j < ldq; j += blockDim.x) qs[j] = j < d ? q[j] : 0.f;
+}
+
+__device__ void leaf_range(const ForestView &F, int t, int b, int *lofs, int *lcnt) {
+    const long long lo = ((long long)b * F.n) >> F.L;
+    const long long hi = ((long long)(b + 1) * F.n) >> F.L;
+    lofs[t] = (int)lo;
+    lcnt[t] = (int)(hi - lo);
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Stage 1: one thread per (query, tree); the query row is read through L1.
+__global__ void k_descend(ForestView F, const float *__restrict__ Q, long long m, int *leaf) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= m * F.T) return;
+    const long long i = g / F.T;
+    const int t = (int)(g - i * F.T);
+    leaf[g] = descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, Q + i * F.d);
+}
+
+// Stage 2: one CTA per query.
+__global__ void k_candidates(ForestView F, const int *__restrict__ leaf, long long m, int *cand,
+                             int *ncand) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem s = carve(smem_raw, F.d, F.T, F.cand_cap);
+    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
+        for (int t = threadIdx.x; t < F.T; t += blockDim.x) {
+            int b = leaf[i * F.T + t];
+            b = min(max(b, 0), (1 << F.L) - 1);
+            leaf_range(F, t, b, s.lofs, s.lcnt);
+        }
+        __syncthreads();
+        const int C = gather_unique(F, s.lofs, s.lcnt, s.lpos, reinterpret_cast<int *>(s.keys), s.u,
+                                    s.wtmp, s.sh);
+        for (int j = threadIdx.x; j < C; j += blockDim.x) cand[(size_t)i * F.cand_cap + j] = s.u[j];
+        if (threadIdx.x == 0) ncand[i] = C;
+        __syncthreads();
+    }
+}
+
+// Stages 3-4 (float32): one CTA per query.
+template <int NC>
+__global__ void k_score_topk(ForestView F, const float *__restrict__ Q, long long m,
+                             const int *__restrict__ cand, const int *__restrict__ ncand, int stride,
+                             int k, long long *ids, float *dists) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem s = carve(smem_raw, F.d, F.T, F.cand_cap);
+    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
+        load_query(Q + i * F.d, F.d, s.qs);
+        const int C = min(max(ncand[i], 0), min(stride, F.cand_cap));
+        for (int j = threadIdx.x; j < C; j += blockDim.x) s.u[j] = cand[(size_t)i * stride + j];
+        __syncthreads();
+        score_rows<P_F32, NC>(F, s.qs, s.u, C, s.keys);
+        sort_keys(s.keys, C);
+        write_topk(s.keys, C, k, ids + i * k, dists + i * k);
+        __syncthreads();
+    }
+}
+
+// Screened distance of every candidate (no selection), for checking the screen arithmetic.
+template <int PREC, int NC>
+__global__ void k_score_all(ForestView F, const float *__restrict__ Q, long long m,
+                            const int *__restrict__ cand, const int *__restrict__ ncand, int stride,
+                            float *out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem s = carve(smem_raw, F.d, F.T, F.cand_cap);
+    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
+        load_query(Q + i * F.d, F.d, s.qs);
+        const int C = min(max(ncand[i], 0), min(stride, F.cand_cap));
+        for (int j = threadIdx.x; j < C; j += blockDim.x) s.u[j] = cand[(size_t)i * stride + j];
+        __syncthreads();
+        score_rows<PREC, NC>(F, s.qs, s.u, C, s.keys);
+        __syncthreads();
+        for (int j = threadIdx.x; j < C; j += blockDim.x)
+            out[(size_t)i * stride + j] = s.keys[j] == KEY_NONE ? __int_as_float(0x7fc00000)
+                                                                 : __uint_as_float((unsigned)(s.keys[j] >> 32));
+        __syncthreads();
+    }
+}
+
+// The whole path per query (persistent: CTAs stride over the queries).  Screened precisions rank
+// the candidates by the low-precision distance, keep the R best and rerank them in float32.
+template <int PREC, int NC, int NCF>
+__global__ void k_query_fused(ForestView F, const float *__restrict__ Q, long long m, int k, int R,
+                              long long *ids, float *dists) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem s = carve(smem_raw, F.d, F.T, F.cand_cap);
+    for (long long i = blockIdx.x; i < m; i += gridDim.x) {
+        load_query(Q + i * F.d, F.d, s.qs);
+        __syncthreads();
+        for (int t = threadIdx.x; t < F.T; t += blockDim.x)
+            leaf_range(F, t, descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, s.qs), s.lofs, s.lcnt);
+        __syncthreads();
+        int C = gather_unique(F, s.lofs, s.lcnt, s.lpos, reinterpret_cast<int *>(s.keys), s.u, s.wtmp,
+                              s.sh);
+        score_rows<PREC, NC>(F, s.qs, s.u, C, s.keys);
+        sort_keys(s.keys, C);
+        if (PREC != P_F32) {
+            // shortlist: the R best by the screened distance, rescored in float32
+            const int Rn = min(R, C);
+            for (int j = threadIdx.x; j < Rn; j += blockDim.x)
+                s.u[j] = (int)(unsigned)(s.keys[j] & 0xffffffffu);
+            __syncthreads();
+            score_rows<P_F32, NCF>(F, s.qs, s.u, Rn, s.keys);
+            sort_keys(s.keys, Rn);
+            C = Rn;
+        }
+        write_topk(s.keys, C, k, ids + i * k, dists + i * k);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+int nc_for(int chunks) {
+    if (chunks <= 32) return 1;
+    if (chunks <= 64) return 2;
+    if (chunks <= 128) return 4;
+    if (chunks <= 256) return 8;
+    return 0;
+}
+
+template <typename KernelT>
+int prep_kernel(KernelT kern, size_t smem) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return gf_cuda_fail(e, "cudaFuncSetAttribute(max dynamic smem)");
+    }
+    return GF_OK;
+}
+
+int check_smem(const gf_forest *F, size_t smem) {
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)lim)
+        return gf_fail(GF_EUNSUPPORTED,
+                       "per-query shared memory %zu B (d=%d, T=%d, candidates<=%d) exceeds %d B",
+                       smem, F->d, F->T, F->cand_cap, lim);
+    return GF_OK;
+}
+
+template <int PREC, int NC, int NCF>
+int launch_fused(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
+                 int ctas_per_sm, cudaStream_t st, int64_t *ids, float *dists) {
+    const size_t smem = smem_bytes(F->d, F->T, F->cand_cap);
+    int r = check_smem(F, smem);
+    if (r) return r;
+    auto kern = k_query_fused<PREC, NC, NCF>;
+    if ((r = prep_kernel(kern, smem))) return r;
+    const int threads = warps * 32;
+    cudaFuncAttributes fa;
+    GF_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    if (threads > fa.maxThreadsPerBlock)
+        return gf_fail(GF_EINVAL, "warps_per_cta=%d exceeds this kernel's limit of %d threads (%d registers)",
+                       warps, fa.maxThreadsPerBlock, fa.numRegs);
+    if (ctas_per_sm <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+        ctas_per_sm = occ > 0 ? occ : 1;
+    }
+    long long grid = (long long)F->num_sms * ctas_per_sm;
+    if (grid > m) grid = m;
+    kern<<<(unsigned)grid, threads, smem, st>>>(view_of(F), Q, m, k, R, (long long *)ids, dists);
+    GF_CUDA_TRY(cudaGetLastError());
+    return GF_OK;
+}
+
+template <int PREC>
+int dispatch_prec(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
+                  int cps, cudaStream_t st, int64_t *ids, float *dists) {
+    const int chunks = PREC == P_F32 ? F->ldx / 4 : PREC == P_BF16 ? F->ldb / 8 : F->ld8 / 16;
+    const int ncf = nc_for(F->ldx / 4);
+    const int nc = nc_for(chunks);
+#define GF_CASE(A, B)                                                                       \
+    if (nc == A && ncf == B) return launch_fused<PREC, A, B>(F, Q, m, k, R, warps, cps, st, ids, dists);
+    if (PREC == P_F32) {
+        GF_CASE(1, 1) GF_CASE(2, 2) GF_CASE(4, 4) GF_CASE(8, 8) GF_CASE(0, 0)
+    } else {
+        // the screened row is shorter than the float32 row, so its class is never larger
+        GF_CASE(1, 1) GF_CASE(1, 2) GF_CASE(1, 4) GF_CASE(2, 4) GF_CASE(2, 8) GF_CASE(4, 8)
+        GF_CASE(1, 8) GF_CASE(4, 0) GF_CASE(8, 0) GF_CASE(0, 0) GF_CASE(2, 0) GF_CASE(1, 0)
+    }
+#undef GF_CASE
+    return gf_fail(GF_EUNSUPPORTED, "no kernel for chunk classes %d/%d", nc, ncf);
+}
+
+}  // namespace
+
+int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,
+                    int32_t R, int32_t warps, int32_t ctas_per_sm, cudaStream_t st, int64_t *ids,
+                    float *dists) {
+    switch (precision) {
+        case GF_FP32: return dispatch_prec<P_F32>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists);
+        case GF_BF16_RERANK: return dispatch_prec<P_BF16>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists);
+        case GF_FP8_RERANK: return dispatch_prec<P_FP8>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists);
+    }
+    return gf_fail(GF_EINVAL, "unknown precision %d", precision);
+}
+
+// ---------------------------------------------------------------- ABI: staged path
+
+extern "C" int gf_descend(const gf_forest *F, const float *Q, int64_t m, int32_t *leaf, void *stream) {
+    if (!F) return gf_fail(GF_EINVAL, "gf_descend: null forest");
+    if (m < 0) return gf_fail(GF_EINVAL, "gf_descend: m < 0");
+    if (m == 0) return GF_OK;
+    if (!Q || !leaf) return gf_fail(GF_EINVAL, "gf_descend: null pointer");
+    const long long tot = (long long)m * F->T;
+    const int threads = 256;
+    k_descend<<<(unsigned)((tot + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(
+        view_of(F), Q, m, leaf);
+    GF_CUDA_TRY(cudaGetLastError());
+    return GF_OK;
+}
+
+extern "C" int gf_candidates(const gf_forest *F, const int32_t *leaf, int64_t m, int32_t *cand,
+                             int32_t *ncand, void *stream) {
+    if (!F) return gf_fail(GF_EINVAL, "gf_candidates: null forest");
+    if (m < 0) return gf_fail(GF_EINVAL, "gf_candidates: m < 0");
+    if (m == 0) return GF_OK;
+    if (!leaf || !cand || !ncand) return gf_fail(GF_EINVAL, "gf_candidates: null pointer");
+    const size_t smem = smem_bytes(F->d, F->T, F->cand_cap);
+    int r = check_smem(F, smem);
+    if (r) return r;
+    if ((r = prep_kernel(k_candidates, smem))) return r;
+    const long long grid = m < (long long)F->num_sms * 8 ? m : (long long)F->num_sms * 8;
+    k_candidates<<<(unsigned)grid, 256, smem, (cudaStream_t)stream>>>(view_of(F), leaf, m, cand, ncand);
+    GF_CUDA_TRY(cudaGetLastError());
+    return GF_OK;
+}
+
+extern "C" int gf_score_topk(const gf_forest *F, const float *Q, int64_t m, const int32_t *cand,
+                             const int32_t *ncand, int32_t cand_stride, int32_t k, int64_t *ids,
+                             float *dists, void *stream) {
+    if (!F) return gf_fail(GF_EINVAL, "gf_score_topk: null forest");
+    if (m < 0 || k < 1 || cand_stride < 0) return gf_fail(GF_EINVAL, "gf_score_topk: bad sizes");
+    if (m == 0) return GF_OK;
+    if (!Q || !cand || !ncand || !ids || !dists) return gf_fail(GF_EINVAL, "gf_score_topk: null pointer");
+    const size_t smem = smem_bytes(F->d, F->T, F->cand_cap);
+    int r = check_smem(F, smem);
+    if (r) return r;
+    const long long grid = m < (long long)F->num_sms * 4 ? m : (long long)F->num_sms * 4;
+    const int nc = nc_for(F->ldx / 4);
+    cudaStream_t st = (cudaStream_t)stream;
+#define GF_SCORE(NCV)                                                                        \
+    if (nc == NCV) {                                                                         \
+        if ((r = prep_kernel(k_score_topk<NCV>, smem))) return r;                           \
+        k_score_topk<NCV><<<(unsigned)grid, 256, smem, st>>>(view_of(F), Q, m, cand, ncand, \
+                                                             cand_stride, k, (long long *)ids, dists); \
+    }
+    GF_SCORE(1) GF_SCORE(2) GF_SCORE(4) GF_SCORE(8) GF_SCORE(0)
+#undef GF_SCORE
+    GF_CUDA_TRY(cudaGetLastError());
+    return GF_OK;
+}
+
+extern "C" int gf_score_screened(const gf_forest *F, const float *Q, int64_t m, const int32_t *cand,
+                                 const int32_t *ncand, int32_t cand_stride, int32_t precision,
+                                 float *dist, void *stream) {
+    if (!F) return gf_fail(GF_EINVAL, "gf_score_screened: null forest");
+    if (m < 0 || cand_stride < 0) return gf_fail(GF_EINVAL, "gf_score_screened: bad sizes");
+    if (m == 0) return GF_OK;
+    if (!Q || !cand || !ncand || !dist) return gf_fail(GF_EINVAL, "gf_score_screened: null pointer");
+    if (precision == GF_BF16_RERANK && !F->xb) return gf_fail(GF_EINVAL, "no bf16 copy");
+    if (precision == GF_FP8_RERANK && !F->x8) return gf_fail(GF_EINVAL, "no fp8 copy");
+    if (precision < 0 || precision > 2) return gf_fail(GF_EINVAL, "unknown precision %d", precision);
+    const size_t smem = smem_bytes(F->d, F->T, F->cand_cap);
+    int r = check_smem(F, smem);
+    if (r) return r;
+    const long long grid = m < (long long)F->num_sms * 4 ? m : (long long)F->num_sms * 4;
+    const int chunks = precision == GF_FP32 ? F->ldx / 4 : precision == GF_BF16_RERANK ? F->ldb / 8 : F->ld8 / 16;
+    const int nc = nc_for(chunks);
+    cudaStream_t st = (cudaStream_t)stream;
+#define GF_ALL(PV, NCV)                                                                          \
+    if (precision == PV && nc == NCV) {                                                          \
+        auto kern = k_score_all<PV, NCV>;                                                        \
+        if ((r = prep_kernel(kern, smem))) return r;                                            \
+        kern<<<(unsigned)grid, 256, smem, st>>>(view_of(F), Q, m, cand, ncand, cand_stride, dist); \
+    }
+    GF_ALL(P_F32, 1) GF_ALL(P_F32, 2) GF_ALL(P_F32, 4) GF_ALL(P_F32, 8) GF_ALL(P_F32, 0)
+    GF_ALL(P_BF16, 1) GF_ALL(P_BF16, 2) GF_ALL(P_BF16, 4) GF_ALL(P_BF16, 8) GF_ALL(P_BF16, 0)
+    GF_ALL(P_FP8, 1) GF_ALL(P_FP8, 2) GF_ALL(P_FP8, 4) GF_ALL(P_FP8, 8) GF_ALL(P_FP8, 0)
+#undef GF_ALL
+    GF_CUDA_TRY(cudaGetLastError());
+    return GF_OK;
+}

@@ -1,0 +1,241 @@
+"""Python binding of the C ABI in include/gf.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device buffers are torch CUDA
+tensors (allocation and streams come from PyTorch); all computation runs in the library's CUDA
+kernels.  If the compiled library is missing, importing this module raises -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import _build
+
+GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ETIMEOUT, GF_EUNSUPPORTED, GF_EIO = 0, -1, -2, -3, -4, -5, -6
+GF_FP32, GF_BF16_RERANK, GF_FP8_RERANK = 0, 1, 2
+GF_VAR_NODE, GF_VAR_GLOBAL = 0, 1
+PRECISIONS = {"fp32": GF_FP32, "bf16": GF_BF16_RERANK, "fp8": GF_FP8_RERANK}
+
+
+class GFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gf error {code}: {msg}")
+        self.code = code
+
+
+class RandParams(C.Structure):
+    _fields_ = [("t", C.c_int32), ("shuffle", C.c_int32), ("var_scope", C.c_int32),
+                ("householder", C.c_int32)]
+
+
+class QueryOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rerank_R", C.c_int32), ("warps_per_cta", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("stream", C.c_void_p)]
+
+
+class ForestInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("T", C.c_int32), ("leaf_size", C.c_int32),
+                ("L", C.c_int32), ("max_leaf", C.c_int32), ("cand_cap", C.c_int32),
+                ("screens", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"CUDA library {_build.LIB} is not built; run __graft_entry__.build()")
+        L = C.CDLL(_build.LIB)
+        P, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+        sig = {
+            "gf_build": ([P, i64, i32, i32, i32, P, u64, P], i32),
+            "gf_build_ex": ([P, i64, i32, i32, i32, P, u64, i32, P, P], i32),
+            "gf_forest_import": ([P, i64, i32, i32, i32, P, P, P, P], i32),
+            "gf_forest_export": ([P, P, P, P], i32),
+            "gf_forest_get_info": ([P, P], i32),
+            "gf_forest_add_screen": ([P, i32, P], i32),
+            "gf_forest_set_tuning": ([P, i32, i32, i32, i32], i32),
+            "gf_forest_free": ([P], i32),
+            "gf_query": ([P, P, i64, i32, P, P], i32),
+            "gf_query_ex": ([P, P, i64, i32, P, P, P], i32),
+            "gf_descend": ([P, P, i64, P, P], i32),
+            "gf_candidates": ([P, P, i64, P, P, P], i32),
+            "gf_score_topk": ([P, P, i64, P, P, i32, i32, P, P, P], i32),
+            "gf_score_screened": ([P, P, i64, P, P, i32, i32, P, P], i32),
+            "gf_last_error": ([], C.c_char_p),
+            "gf_version": ([], i32),
+            "gf_rand_params_default": ([P], None),
+            "gf_query_opts_default": ([P], None),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(code: int) -> None:
+    if code != GF_OK:
+        raise GFError(code, lib().gf_last_error().decode())
+
+
+def _dptr(t: torch.Tensor, dtype: torch.dtype, name: str) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Forest:
+    """Owner of a gf_forest handle."""
+
+    def __init__(self, handle: C.c_void_p):
+        self.handle = handle
+        self._info = None
+
+    @property
+    def info(self) -> ForestInfo:
+        inf = ForestInfo()
+        _check(lib().gf_forest_get_info(self.handle, C.byref(inf)))
+        return inf
+
+    def free(self) -> None:
+        if self.handle:
+            _check(lib().gf_forest_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def gf_rand_params(t: int = 5, shuffle: int = 1, var_scope: int = GF_VAR_NODE,
+                   householder: int = 0) -> RandParams:
+    return RandParams(t, shuffle, var_scope, householder)
+
+
+def gf_build(X: torch.Tensor, T: int, leaf_size: int, t: int = 5, shuffle: int = 1,
+             var_scope: int = GF_VAR_NODE, seed: int = 0, householder: int = 0,
+             borrow_x: bool = False, stream=None) -> Forest:
+    n, d = X.shape
+    rp = gf_rand_params(t, shuffle, var_scope, householder)
+    h = C.c_void_p()
+    _check(lib().gf_build_ex(_dptr(X, torch.float32, "X"), n, d, T, leaf_size, C.byref(rp),
+                             seed & (2**64 - 1), int(borrow_x), _stream(stream), C.byref(h)))
+    f = Forest(h)
+    if borrow_x:
+        f._x = X  # keep the borrowed points alive
+    return f
+
+
+def gf_forest_import(X: torch.Tensor, T: int, leaf_size: int, split_dim, split_val, perm) -> Forest:
+    import numpy as np
+    n, d = X.shape
+    sd = np.ascontiguousarray(split_dim, dtype=np.int32)
+    sv = np.ascontiguousarray(split_val, dtype=np.float32)
+    pm = np.ascontiguousarray(perm, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().gf_forest_import(_dptr(X, torch.float32, "X"), n, d, T, leaf_size,
+                                  sd.ctypes.data, sv.ctypes.data, pm.ctypes.data, C.byref(h)))
+    return Forest(h)
+
+
+def gf_forest_export(F: Forest):
+    import numpy as np
+    inf = F.info
+    nn = (1 << inf.L) - 1
+    sd = np.empty((inf.T, nn), dtype=np.int32)
+    sv = np.empty((inf.T, nn), dtype=np.float32)
+    pm = np.empty((inf.T, inf.n), dtype=np.int32)
+    _check(lib().gf_forest_export(F.handle, sd.ctypes.data, sv.ctypes.data, pm.ctypes.data))
+    return sd, sv, pm
+
+
+def gf_forest_add_screen(F: Forest, precision: int, stream=None) -> None:
+    _check(lib().gf_forest_add_screen(F.handle, precision, _stream(stream)))
+
+
+def gf_forest_set_tuning(F: Forest, precision: int, warps_per_cta: int, ctas_per_sm: int,
+                         rerank_R: int) -> None:
+    _check(lib().gf_forest_set_tuning(F.handle, precision, warps_per_cta, ctas_per_sm, rerank_R))
+
+
+def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, rerank_R: int = 0,
+             warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None,
+             out: tuple[torch.Tensor, torch.Tensor] | None = None):
+    """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k])."""
+    m = Q.shape[0]
+    if out is None:
+        ids = torch.empty((m, k), dtype=torch.int64, device=Q.device)
+        dists = torch.empty((m, k), dtype=torch.float32, device=Q.device)
+    else:
+        ids, dists = out
+    o = QueryOpts(precision, rerank_R, warps_per_cta, ctas_per_sm, _stream(stream))
+    _check(lib().gf_query_ex(F.handle, _dptr(Q, torch.float32, "Q"), m, k, C.byref(o),
+                             _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists")))
+    return ids, dists
+
+
+def gf_descend(F: Forest, Q: torch.Tensor, stream=None) -> torch.Tensor:
+    m = Q.shape[0]
+    leaf = torch.empty((m, F.info.T), dtype=torch.int32, device=Q.device)
+    _check(lib().gf_descend(F.handle, _dptr(Q, torch.float32, "Q"), m, _dptr(leaf, torch.int32, "leaf"),
+                            _stream(stream)))
+    return leaf
+
+
+def gf_candidates(F: Forest, leaf: torch.Tensor, stream=None):
+    m = leaf.shape[0]
+    cap = F.info.cand_cap
+    cand = torch.empty((m, cap), dtype=torch.int32, device=leaf.device)
+    ncand = torch.empty((m,), dtype=torch.int32, device=leaf.device)
+    _check(lib().gf_candidates(F.handle, _dptr(leaf, torch.int32, "leaf"), m,
+                               _dptr(cand, torch.int32, "cand"), _dptr(ncand, torch.int32, "ncand"),
+                               _stream(stream)))
+    return cand, ncand
+
+
+def gf_score_topk(F: Forest, Q: torch.Tensor, cand: torch.Tensor, ncand: torch.Tensor, k: int,
+                  stream=None):
+    m = Q.shape[0]
+    ids = torch.empty((m, k), dtype=torch.int64, device=Q.device)
+    dists = torch.empty((m, k), dtype=torch.float32, device=Q.device)
+    _check(lib().gf_score_topk(F.handle, _dptr(Q, torch.float32, "Q"), m,
+                               _dptr(cand, torch.int32, "cand"), _dptr(ncand, torch.int32, "ncand"),
+                               cand.shape[1], k, _dptr(ids, torch.int64, "ids"),
+                               _dptr(dists, torch.float32, "dists"), _stream(stream)))
+    return ids, dists
+
+
+def gf_score_screened(F: Forest, Q: torch.Tensor, cand: torch.Tensor, ncand: torch.Tensor,
+                      precision: int, stream=None) -> torch.Tensor:
+    m = Q.shape[0]
+    dist = torch.full(cand.shape, float("nan"), dtype=torch.float32, device=Q.device)
+    _check(lib().gf_score_screened(F.handle, _dptr(Q, torch.float32, "Q"), m,
+                                   _dptr(cand, torch.int32, "cand"), _dptr(ncand, torch.int32, "ncand"),
+                                   cand.shape[1], precision, _dptr(dist, torch.float32, "dist"),
+                                   _stream(stream)))
+    return dist
+
+
+def gf_version() -> int:
+    return lib().gf_version()

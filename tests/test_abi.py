@@ -1,0 +1,57 @@
+"""The C library loads and exports every entry point include/gf.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gf_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+    from paper_1603_09596_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for must in ("gf_build", "gf_query", "gf_query_ex", "gf_descend", "gf_candidates", "gf_score_topk",
+                 "gf_forest_free", "gf_forest_import", "gf_forest_export", "gf_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_reports_errors_without_a_gpu(libpath):
+    import paper_1603_09596_gb300 as gf
+    lib = gf.lib()
+    assert lib.gf_version() >= 100
+    # argument validation happens before any device work
+    assert lib.gf_query(None, None, 1, 1, None, None) == gf.GF_EINVAL
+    assert b"null" in lib.gf_last_error()
+    assert lib.gf_build(None, 10, 4, 2, 4, None, 0, None) == gf.GF_EINVAL
+
+
+def test_oracle_is_not_imported_by_the_package():
+    pkg = os.path.join(ROOT, "paper_1603_09596_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "gf_oracle" not in txt, f

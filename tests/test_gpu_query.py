@@ -1,0 +1,239 @@
+"""GPU query path against the CPU oracle on the same forest (Alg. 2 with one leaf per tree).
+
+The forest is built by the oracle and imported into the GPU library, so both sides search the
+identical structure.  Leaves and candidate sets must match bit for bit; float32 distances within
+1e-5 relative of float64; k-NN ids exactly except at near-ties.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import screen
+from parity import RTOL, assert_topk_close, candidate_sets
+
+pytestmark = pytest.mark.gpu
+
+# (name, n, d, m, T, leaf_size, law): the tiny workload, ragged sizes (d not a multiple of 4/8/16,
+# m and n odd), more trees than a warp, a row longer than the register-resident query, and the
+# 960-d GIST-like law.
+CASES = [
+    ("tiny", 10_000, 128, 100, 8, 32, "A"),
+    ("ragged", 3001, 37, 57, 5, 9, "B"),
+    ("manytrees", 5000, 64, 40, 40, 16, "A"),
+    ("long_rows", 3000, 2000, 30, 6, 40, "C"),
+    ("gist_like", 20_000, 960, 200, 16, 64, "B"),
+]
+
+
+@pytest.fixture(scope="module")
+def gf():
+    import paper_1603_09596_gb300 as g
+    g.lib()
+    return g
+
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        spec = next(c for c in CASES if c[0] == name)
+        _, n, d, m, T, p, law = spec
+        X, Q = synth.mixture(n, d, m, law, seed=0, qseed=1)
+        F = oracle.build_forest(X, T, p, t=min(5, d), seed=7)
+        _cache[name] = (X, Q, F)
+    return _cache[name]
+
+
+def gpu_forest(gf, X, F):
+    Xg = torch.from_numpy(X).cuda()
+    return gf.gf_forest_import(Xg, F.T, F.leaf_size, F.split_dim, F.split_val, F.perm), Xg
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_descend_bit_exact(gf, name):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    leaf = gf.gf_descend(G, torch.from_numpy(Q).cuda()).cpu().numpy()
+    assert np.array_equal(leaf, oracle.descend(F, Q))
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_candidates_bit_exact(gf, name):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    leaf = oracle.descend(F, Q)
+    cand, nc = gf.gf_candidates(G, torch.from_numpy(leaf).cuda())
+    cand, nc = cand.cpu().numpy(), nc.cpu().numpy()
+    offs, ids = oracle.candidates(F, leaf)
+    assert np.array_equal(nc, np.diff(offs))
+    for i in range(Q.shape[0]):
+        assert np.array_equal(cand[i, :nc[i]], ids[offs[i]:offs[i + 1]])
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_score_topk(gf, name):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    m = Q.shape[0]
+    width = int(np.diff(offs).max())
+    cand = np.zeros((m, width), dtype=np.int32)
+    for i in range(m):
+        cand[i, :offs[i + 1] - offs[i]] = ids[offs[i]:offs[i + 1]]
+    k = 10
+    gi, gd = gf.gf_score_topk(G, torch.from_numpy(Q).cuda(), torch.from_numpy(cand).cuda(),
+                              torch.from_numpy(np.diff(offs).astype(np.int32)).cuda(), k)
+    oi, od = oracle.topk(X, Q, offs, ids, k)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("k", [1, 10])
+def test_query_fused_fp32(gf, name, k):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k)
+    torch.cuda.synchronize()
+    oi, od = oracle.search(F, X, Q, k)
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+
+
+@pytest.mark.parametrize("warps,cps", [(1, 1), (4, 2), (8, 3), (16, 1)])
+def test_query_kernel_shapes_agree(gf, warps, cps):
+    X, Q, F = case("gist_like")
+    G, _ = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    ref_i, ref_d = gf.gf_query(G, Qg, 10)
+    gi, gd = gf.gf_query(G, Qg, 10, warps_per_cta=warps, ctas_per_sm=cps)
+    # the distance of a row does not depend on the CTA shape: bit-identical results
+    assert torch.equal(gi, ref_i) and torch.equal(gd, ref_d)
+
+
+def test_query_pads_short_candidate_lists(gf):
+    X, Q = synth.mixture(64, 8, 5, "A", seed=3)
+    F = oracle.build_forest(X, 1, 4, seed=0)
+    G, _ = gpu_forest(gf, X, F)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 6)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    oi, od = oracle.search(F, X, Q, 6)
+    assert np.all(gi[:, 4:] == -1) and np.all(np.isinf(gd[:, 4:]))
+    assert_topk_close(X, Q, gi, gd, oi, od)
+
+
+def test_query_single_leaf_is_exact_knn(gf):
+    # leaf_size >= n: one leaf holds every point, so the search is brute force
+    X, Q = synth.mixture(500, 33, 25, "B", seed=4)
+    F = oracle.build_forest(X, 2, 500, seed=0)
+    G, _ = gpu_forest(gf, X, F)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 7)
+    ei, ed = oracle.bruteforce(X, Q, 7)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), ei, ed)
+
+
+def test_query_edge_sizes(gf):
+    X, Q, F = case("ragged")
+    G, _ = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    e = gf.gf_query(G, Qg[:0], 3)
+    assert e[0].shape == (0, 3)
+    gi, gd = gf.gf_query(G, Qg[:1], 3)
+    oi, od = oracle.search(F, X, Q[:1], 3)
+    assert_topk_close(X, Q[:1], gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+    with pytest.raises(gf.GFError):
+        gf.gf_query(G, Qg, 0)
+
+
+def test_query_on_side_stream(gf):
+    X, Q, F = case("tiny")
+    G, _ = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        gi, gd = gf.gf_query(G, Qg, 5, stream=s)
+    s.synchronize()
+    oi, od = oracle.search(F, X, Q, 5)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+
+
+# ---------------------------------------------------------------- screened precisions
+
+def assert_screened_close(X, Q, gi, gd, oi, od, cands, max_frac=0.03):
+    """Like assert_topk_close, but a row may also differ where the float32 screen and the float64
+    screen order the shortlist boundary differently; every reported id must still be a candidate
+    reported with its exact distance, and such rows must be rare."""
+    m, k = oi.shape
+    bad = 0
+    for i in range(m):
+        fin = oi[i] >= 0
+        assert np.array_equal(gi[i] >= 0, fin)
+        if np.array_equal(gi[i], oi[i]):
+            np.testing.assert_allclose(gd[i][fin], od[i][fin], rtol=RTOL)
+            continue
+        bad += 1
+        for j in np.nonzero(fin)[0]:
+            gid = int(gi[i, j])
+            assert gid in cands[i]
+            true = oracle.dist2(Q[i], X[gid])
+            assert abs(true - gd[i, j]) <= RTOL * max(true, 1e-30)
+        assert np.all(np.diff(gd[i][fin]) >= 0)
+    assert bad <= max(1, int(max_frac * m)), f"{bad} of {m} rows differ"
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("name", ["tiny", "ragged", "long_rows", "gist_like"])
+def test_query_screened(gf, prec, name):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    gf.gf_forest_add_screen(G, gf.PRECISIONS[prec])
+    R, k = 32, 10
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.PRECISIONS[prec], rerank_R=R)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    oi, od, _ = screen.screened_search(F, X, Q, k, R, prec, offs, ids)
+    assert_screened_close(X, Q, gi, gd, oi, od, candidate_sets(offs, ids))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_screened_full_shortlist_equals_fp32(gf, prec):
+    # R >= every candidate count: the rerank sees every candidate, so the answer is the float32 one
+    X, Q, F = case("tiny")
+    G, _ = gpu_forest(gf, X, F)
+    gf.gf_forest_add_screen(G, gf.PRECISIONS[prec])
+    Qg = torch.from_numpy(Q).cuda()
+    fi, fd = gf.gf_query(G, Qg, 10)
+    si, sd = gf.gf_query(G, Qg, 10, precision=gf.PRECISIONS[prec], rerank_R=G.info.cand_cap)
+    assert torch.equal(fi, si) and torch.equal(fd, sd)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("name", ["ragged", "long_rows", "gist_like"])
+def test_screened_distances_elementwise(gf, prec, name):
+    # every candidate's screened distance against the float64 value of the same rounded points
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    if prec != "fp32":
+        gf.gf_forest_add_screen(G, gf.PRECISIONS[prec])
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    m = Q.shape[0]
+    width = int(np.diff(offs).max())
+    cand = np.zeros((m, width), dtype=np.int32)
+    for i in range(m):
+        cand[i, :offs[i + 1] - offs[i]] = ids[offs[i]:offs[i + 1]]
+    nc = np.diff(offs).astype(np.int32)
+    dist = gf.gf_score_screened(G, torch.from_numpy(Q).cuda(), torch.from_numpy(cand).cuda(),
+                                torch.from_numpy(nc).cuda(), gf.PRECISIONS[prec]).cpu().numpy()
+    if prec == "fp32":
+        deq = X.astype(np.float64)
+    elif prec == "bf16":
+        deq = screen.bf16_round(X).astype(np.float64)
+    else:
+        sc, codes = screen.fp8_quantize(X)
+        deq = codes * sc.astype(np.float64)[:, None]
+    for i in range(m):
+        c = cand[i, :nc[i]]
+        ref = ((deq[c] - Q[i].astype(np.float64)) ** 2).sum(axis=1)
+        np.testing.assert_allclose(dist[i, :nc[i]], ref, rtol=RTOL, atol=RTOL * ref.max())
