@@ -60,7 +60,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -131,6 +131,7 @@ def recall(torch, Xg, Qs, ids, exact_i, exact_d):
 def ours(args):
     import torch
     import paper_1603_09596_gb300 as gf
+    from paper_1603_09596_gb300 import autotune
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -150,24 +151,15 @@ def ours(args):
     Qg = torch.from_numpy(Q).to(dev)
     stream = torch.cuda.current_stream(dev)
     hbm_peak, peak_kind = peaks()
-    res = {}
 
-    def build(T, p):
-        torch.cuda.synchronize()
-        t = time.time()
-        F = gf.gf_build(Xg, T, p, seed=0)
-        torch.cuda.synchronize()
-        return F, time.time() - t
-
-    # exact neighbours of a query sample, for recall
     S = min(m, args.recall_sample)
     ei, ed = exact_nn(torch, Xg, Qg[:S], k)
 
-    def time_query(F, prec, R, steps, warmup):
+    def time_query(F, prec, steps, warmup):
         ids = torch.empty((m, k), dtype=torch.int64, device=dev)
         dd = torch.empty((m, k), dtype=torch.float32, device=dev)
         for _ in range(warmup):
-            gf.gf_query(F, Qg, k, precision=prec, rerank_R=R, out=(ids, dd))
+            gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd))
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -176,113 +168,114 @@ def ours(args):
             torch.cuda.synchronize()
             for a, b in evs:
                 a.record(stream)
-                gf.gf_query(F, Qg, k, precision=prec, rerank_R=R, out=(ids, dd))
+                gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd))
                 b.record(stream)
             torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in evs]
         return ids, dd, ms, ck.summary()
 
-    def candidates_per_query(F):
-        leaf = gf.gf_descend(F, Qg)
-        try:
-            _, nc = gf.gf_candidates(F, leaf)
-            return float(nc.double().mean())
-        except gf.GFError:
-            return None
+    def bytes_per_query(F, prec, C, R):
+        inf = F.info
+        positions = inf.T * (n / (1 << inf.L))       # leaf ids read from the permutations
+        rows = C * d * (2 if prec == gf.GF_BF16_RERANK else 4)
+        rerank = R * d * 4 if prec != gf.GF_FP32 else 0
+        return rows + rerank + d * 4 + positions * 4 + 12 * k
 
-    out = {}
-    for name, par in (("headline", HEADLINE), ("spec", SPEC)):
-        F, bs = build(par["T"], par["leaf_size"])
+    def run_forest(T, p, tune_sample):
+        torch.cuda.synchronize()
+        tb = time.time()
+        F = gf.gf_build(Xg, T, p, seed=0)
+        torch.cuda.synchronize()
+        entry = {"T": T, "leaf_size": p, "L": F.info.L, "build_s": round(time.time() - tb, 3)}
         gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
-        entry = {"T": par["T"], "leaf_size": par["leaf_size"], "L": F.info.L, "build_s": round(bs, 3)}
-        for prec_name, prec, R in (("bf16", gf.GF_BF16_RERANK, args.R), ("fp32", gf.GF_FP32, 0)):
-            try:
-                ids, dd, ms, ck = time_query(F, prec, R, args.steps, args.warmup)
-            except gf.GFError as e:
-                entry[prec_name] = {"error": str(e)}
-                continue
+        nc = torch.empty((m,), dtype=torch.int32, device=dev)
+        gf.gf_query(F, Qg, k, algo=gf.GF_ALGO_STREAM, ncand_out=nc)
+        C = float(nc.double().mean())
+        entry["cand_per_query"] = round(C, 1)
+        for name, prec in (("fp32", gf.GF_FP32), ("bf16", gf.GF_BF16_RERANK)):
+            tr = autotune.tune(F, Qg[:tune_sample], k, prec)
+            ids, dd, ms, ck = time_query(F, prec, args.steps, args.warmup)
             r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
             mean_ms = statistics.mean(ms)
-            entry[prec_name] = {"qps": m / (mean_ms / 1e3), "ms_per_step": mean_ms,
-                                "ms_min": min(ms), "recall_at_1": r1, "recall_at_10": rk, "clocks": ck,
-                                "R": R}
-        entry["cand_per_query"] = candidates_per_query(F)
-        out[name] = (entry, F)
-    head, Fh = out["headline"]
-    spec, Fs = out["spec"]
-    best = head.get("bf16", {})
-    if "qps" not in best:
-        best = spec.get("bf16", {})
-    mean_ms = best.get("ms_per_step", float("nan"))
+            R = tr.get("R", 0)
+            bpq = bytes_per_query(F, prec, C, R)
+            entry[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4),
+                           "ms_min": round(min(ms), 4), "recall_at_1": r1, "recall_at_10": rk, "clocks": ck,
+                           "R": R, "warps_per_cta": tr["warps"], "ctas_per_sm": tr["ctas_per_sm"],
+                           "bytes_per_query": round(bpq),
+                           "achieved_gbs": round(bpq * m / (mean_ms / 1e3) / 1e9, 1)}
+        return F, entry
+
+    Fh, head = run_forest(HEADLINE["T"], HEADLINE["leaf_size"], args.tune_sample)
+    if not args.skip_spec:
+        Fs, spec = run_forest(SPEC["T"], SPEC["leaf_size"], args.tune_sample)
+        Fs.free()
+    else:
+        spec = None
+    best = head["bf16"]
+    mean_ms = best["ms_per_step"]
     if world > 1:
         t = torch.tensor([mean_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         mean_ms = float(t.item())
     value = world * m / (mean_ms / 1e3)
-
-    # roofline of the query kernel (one launch per step): algorithmic bytes per launch
-    C = head.get("cand_per_query") or 0.0
-    R = args.R
-    bx = 2  # bf16 screen rows
-    per_q = C * (d * bx) + R * d * 4 + d * 4 + C * 4 + 4 * head["T"] * 0 + 12 * k
-    achieved = per_q * m / (mean_ms / 1e3) / 1e9
+    achieved = best["bytes_per_query"] * m / (mean_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind,
-            "kernel": "k_query (bf16 screen + fp32 rerank)", "bytes_per_query": round(per_q)}
+            "frac": round(achieved / hbm_peak, 4), "traffic": None,
+            "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "kernel": "k_query_stream<bf16> (descent + bitmap dedupe + bf16 screen + fp32 rerank + top-k), 1 launch/step",
+            "bytes_per_query": best["bytes_per_query"]}
 
     # end to end through the public API with host buffers
-    e2e = None
-    if rank == 0 or True:
-        Qh = torch.from_numpy(Q).pin_memory()
-        ih = torch.empty((m, k), dtype=torch.int64).pin_memory()
-        dh = torch.empty((m, k), dtype=torch.float32).pin_memory()
-        Qd = torch.empty_like(Qg)
-        ids = torch.empty((m, k), dtype=torch.int64, device=dev)
-        dd = torch.empty((m, k), dtype=torch.float32, device=dev)
-        prec = gf.GF_BF16_RERANK
-        F = Fh if "qps" in head.get("bf16", {}) else Fs
-        for _ in range(args.warmup):
-            Qd.copy_(Qh, non_blocking=True)
-            gf.gf_query(F, Qd, k, precision=prec, rerank_R=R, out=(ids, dd))
-            ih.copy_(ids, non_blocking=True)
-            dh.copy_(dd, non_blocking=True)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            Qd.copy_(Qh, non_blocking=True)
-            gf.gf_query(F, Qd, k, precision=prec, rerank_R=R, out=(ids, dd))
-            ih.copy_(ids, non_blocking=True)
-            dh.copy_(dd, non_blocking=True)
-        b.record(stream)
-        torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b) / args.steps
-        e2e = {"value": world * m / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": m * d * 4,
-               "d2h_bytes_per_step": m * k * 12}
+    Qh = torch.from_numpy(Q).pin_memory()
+    ih = torch.empty((m, k), dtype=torch.int64).pin_memory()
+    dh = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    Qd = torch.empty_like(Qg)
+    ids = torch.empty((m, k), dtype=torch.int64, device=dev)
+    dd = torch.empty((m, k), dtype=torch.float32, device=dev)
 
-    # CPU oracle on this host's cores, on a bounded sample of the same workload
+    def e2e_step():
+        Qd.copy_(Qh, non_blocking=True)
+        gf.gf_query(Fh, Qd, k, precision=gf.GF_BF16_RERANK, out=(ids, dd))
+        ih.copy_(ids, non_blocking=True)
+        dh.copy_(dd, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e_ms = a.elapsed_time(b) / args.steps
+    e2e = {"value": round(world * m / (e_ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": m * d * 4,
+           "d2h_bytes_per_step": m * k * 12}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(X, Q, Fs if "qps" not in head.get("bf16", {}) else Fh, gf, k, budget_s=args.cpu_budget)
+        cpu = cpu_baseline(X, Q, Fh, gf, k, budget_s=args.cpu_budget)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(mean_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"law-B Gaussian mixture n={n} d={d}, m={m} queries, k={k}",
-                   "T": HEADLINE["T"], "leaf_size": HEADLINE["leaf_size"], "precision": "bf16 screen + fp32 rerank",
-                   "R": R, "recall_at_1": best.get("recall_at_1"), "recall_sample": S,
-                   "l2": "inputs larger than L2 (points 3.84 GB)", "parallelism": f"replicas x{world}"},
+                   "T": HEADLINE["T"], "leaf_size": HEADLINE["leaf_size"],
+                   "precision": "bf16 screen + fp32 rerank", "R": best["R"],
+                   "recall_at_1": best["recall_at_1"], "recall_sample": S,
+                   "l2": "inputs larger than L2 (points 3.84 GB fp32 + 1.92 GB bf16)",
+                   "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * 1,
-        "clocks": best.get("clocks"),
-        "fp32_plain": head.get("fp32"),
-        "bf16_screen": head.get("bf16"),
+        "gpu_launches": args.steps,
+        "clocks": best["clocks"],
+        "fp32_plain": head["fp32"],
+        "bf16_screen": head["bf16"],
+        "headline_forest": {kk: head[kk] for kk in ("T", "leaf_size", "L", "build_s", "cand_per_query")},
         "at_T32_p64": spec,
-        "headline_forest": {"T": head["T"], "leaf_size": head["leaf_size"], "L": head["L"],
-                            "build_s": head["build_s"], "cand_per_query": head.get("cand_per_query")},
         "gen_s": round(gen_s, 2),
         "p99_ms": None,
     }
@@ -306,6 +299,32 @@ def cpu_baseline(X, Q, F, gf, k, budget_s=15.0):
     el = time.time() - t0
     return {"value": round(done / el, 2), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{done} of the {Q.shape[0]} queries, same forest (T={inf.T}, leaf_size={inf.leaf_size}), float64"}
+
+
+def profile(args):
+    """Fixed launches for ncu: build, one warm-up query, then --steps query launches."""
+    import torch
+    import paper_1603_09596_gb300 as gf
+    import synth
+    X, Q = synth.mixture(args.n, args.d, args.m, "B", seed=0, qseed=1)
+    Xg, Qg = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    F = gf.gf_build(Xg, args.T, args.leaf_size, seed=0)
+    prec = gf.PRECISIONS[args.precision]
+    if prec:
+        gf.gf_forest_add_screen(F, prec)
+    kw = dict(precision=prec, rerank_R=args.profile_R, warps_per_cta=args.profile_warps,
+              ctas_per_sm=args.profile_ctas, algo=gf.GF_ALGO_STREAM)
+    gf.gf_query(F, Qg, 10, **kw)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        gf.gf_query(F, Qg, 10, **kw)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": True, "n": args.n, "d": args.d, "m": args.m, "T": args.T,
+                      "leaf_size": args.leaf_size, "precision": args.precision,
+                      "ms_per_launch": a.elapsed_time(b) / args.steps}))
 
 
 def reference(args):
@@ -349,19 +368,29 @@ def reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--d", type=int, default=960)
     ap.add_argument("--m", type=int, default=10_000)
-    ap.add_argument("--R", type=int, default=64)
     ap.add_argument("--recall-sample", type=int, default=1000)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--skip-spec", action="store_true")
+    ap.add_argument("--tune-sample", type=int, default=2000)
+    ap.add_argument("--profile", action="store_true", help="fixed query launches for ncu")
+    ap.add_argument("--T", type=int, default=HEADLINE["T"])
+    ap.add_argument("--leaf-size", type=int, default=HEADLINE["leaf_size"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--profile-R", type=int, default=16)
+    ap.add_argument("--profile-warps", type=int, default=4)
+    ap.add_argument("--profile-ctas", type=int, default=0)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        profile(args)
+    elif args.impl == "reference":
         reference(args)
     else:
         ours(args)

@@ -14,8 +14,8 @@
  *    import, export and free are synchronous.
  *  - Every function returns GF_OK (0) or a negative GF_E* code; no C++ exception crosses the ABI.
  *    gf_last_error() returns a message for the calling thread's most recent failure.
- *  - A const forest may be queried from several host threads at once (queries allocate nothing
- *    and write only to their own outputs).
+ *  - A const forest may be queried from several host threads at once (a query writes only to its
+ *    own outputs and its own scratch).
  *
  * Tree layout (readings of the paper stated once here and used throughout):
  *  - Trees are perfect (Sec. 3 "Tree structure"): depth L = min{l >= 0 : ceil(n / 2^l) <= p} for
@@ -61,12 +61,28 @@ typedef struct gf_rand_params {
 #define GF_BF16_RERANK 1  /* bfloat16 screen -> shortlist of R -> float32 rerank */
 #define GF_FP8_RERANK 2   /* FP8-E4M3 (per-row float32 scale) screen -> R -> float32 rerank */
 
+/* Query kernel.  Both give the same results (same distances, same (distance, id) order). */
+#define GF_ALGO_AUTO 0   /* SORT for small candidate bounds, STREAM otherwise */
+#define GF_ALGO_SORT 1   /* candidates sorted and de-duplicated in shared memory; needs
+                            8 * next_pow2(T * max_leaf) bytes of shared memory per CTA */
+#define GF_ALGO_STREAM 2 /* candidates de-duplicated through a per-CTA bitmap over the point ids
+                            in device memory ("seen" array, Sec. 2.3); any candidate count */
+
 typedef struct gf_query_opts {
-    int32_t precision;     /* GF_FP32, GF_BF16_RERANK or GF_FP8_RERANK */
-    int32_t rerank_R;      /* shortlist length for the screened precisions; 0 = forest default */
-    int32_t warps_per_cta; /* kernel shape; 0 = forest default (set by gf_autotune) */
-    int32_t ctas_per_sm;   /* kernel shape; 0 = forest default (set by gf_autotune) */
-    void *stream;          /* cudaStream_t */
+    int32_t precision;       /* GF_FP32, GF_BF16_RERANK or GF_FP8_RERANK */
+    int32_t rerank_R;        /* shortlist length for the screened precisions; 0 = forest default */
+    int32_t warps_per_cta;   /* kernel shape; 0 = forest default (set by gf_forest_set_tuning) */
+    int32_t ctas_per_sm;     /* kernel shape; 0 = forest default, else occupancy limit */
+    void *stream;            /* cudaStream_t */
+    int32_t algo;            /* GF_ALGO_* */
+    int32_t reserved;
+    void *workspace;         /* STREAM only: device scratch of at least gf_query_workspace_size()
+                                bytes, zero-filled before its first use (every query leaves it zero
+                                again); NULL = the library allocates it stream-ordered
+                                (cudaMallocAsync / cudaFreeAsync) for this call */
+    int64_t workspace_bytes; /* size of `workspace` */
+    int32_t *ncand_out;      /* STREAM only, optional: device [m] int32, number of distinct
+                                candidates of each query */
 } gf_query_opts;
 
 typedef struct gf_forest gf_forest; /* opaque; owned by the library */
@@ -156,7 +172,8 @@ int gf_forest_free(gf_forest *F);
  *          than k candidates
  *   dists  device [m][k] float32: squared L2 distances (float32 arithmetic); +inf with id -1
  * Precision GF_FP32 on the legacy default stream.  m = 0 is a no-op.  Queries containing NaN give
- * unspecified ids but never read or write out of bounds.
+ * unspecified ids but never read or write out of bounds.  The streaming kernel allocates its
+ * scratch stream-ordered unless gf_query_ex is given a workspace.
  * Errors: GF_EINVAL (k < 1, m < 0, null pointers), GF_ECUDA.
  */
 int gf_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int64_t *ids, float *dists);
@@ -166,6 +183,10 @@ int gf_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int64_t *
  * distances.  k must not exceed the shortlist R for screened precisions. */
 int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_t k, const gf_query_opts *o,
                 int64_t *ids, float *dists);
+
+/* Bytes of device scratch a GF_ALGO_STREAM query of m rows needs with these options (one bitmap
+ * of ceil(n / 32) words per CTA of the launch).  o may be NULL for the defaults. */
+int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_query_opts *o, int64_t *bytes);
 
 /* ---------------------------------------------------------------- the path in stages
  * The same computation as gf_query, one step per call, with the intermediate results in caller
@@ -198,6 +219,76 @@ int gf_score_topk(const gf_forest *F, const float *Q, int64_t m, const int32_t *
 int gf_score_screened(const gf_forest *F, const float *Q, int64_t m, const int32_t *cand,
                       const int32_t *ncand, int32_t cand_stride, int32_t precision, float *dist,
                       void *stream);
+
+/* ---------------------------------------------------------------- serving loop
+ * Continuous batching of single-query requests over several resident forests (no counterpart in
+ * the paper, whose search is one query at a time, Sec. 3 "Parallelization"; batched queries are
+ * its stated future work, Sec. 5).
+ *
+ * A server owns `slots` batch slots, each with its own CUDA stream and every buffer a batch needs
+ * (pinned staging, device queries/results, the streaming kernel's workspace), all reserved at
+ * creation.  The number of slots is min(opts.slots, hbm_budget_bytes / bytes_per_slot): that is the
+ * HBM admission rule -- a batch is dispatched exactly when a slot and its memory are free.  A
+ * dispatcher thread takes up to max_batch requests of the forest whose oldest request waited
+ * longest; batches on different slots overlap on the device; requests arriving meanwhile join the
+ * next batch.  Every request's answer equals gf_query on that query alone (same kernel, same
+ * arithmetic).  The forests must outlive the server and must not be freed while it runs.
+ */
+typedef struct gf_server gf_server;
+
+typedef struct gf_server_opts {
+    int32_t max_batch;         /* requests per batch (default 1024) */
+    int32_t slots;             /* batch slots, i.e. batches in flight at most (default 4) */
+    int64_t hbm_budget_bytes;  /* device memory the slots may reserve (default 4 GiB) */
+    int32_t k_max;             /* largest k a request may ask for (default 10) */
+    int32_t precision;         /* GF_FP32 / GF_BF16_RERANK / GF_FP8_RERANK for every batch */
+    int32_t rerank_R;          /* shortlist for the screened precisions (0 = forest default) */
+    int32_t reserved;
+} gf_server_opts;
+
+typedef struct gf_server_stats {
+    int64_t completed;    /* requests finished since the last reset */
+    int64_t batches;      /* batches launched */
+    double mean_batch;    /* requests per batch */
+    double p50_ms;        /* latency, submission to completion */
+    double p99_ms;
+    double max_ms;
+    double span_s;        /* first submission to last completion */
+    double qps;           /* completed / span_s */
+    int32_t slots;
+    int32_t reserved;
+} gf_server_stats;
+
+void gf_server_opts_default(gf_server_opts *o);
+
+/* Errors: GF_EINVAL (no forests, a forest without the screening copy `precision` needs, bad
+ * options), GF_ENOMEM (the budget holds no slot, or an allocation failed), GF_ECUDA. */
+int gf_server_create(gf_forest *const *forests, int32_t nforests, const gf_server_opts *opts,
+                     gf_server **out);
+int gf_server_slots(const gf_server *S);
+
+/* Queue one query (host [d] float32 of the forest's d, copied) for forest index `forest` with
+ * 1 <= k <= k_max; *ticket identifies it.  Thread-safe, non-blocking. */
+int gf_server_submit(gf_server *S, int32_t forest, const float *q_host, int32_t k, uint64_t *ticket);
+
+/* Wait up to timeout_us for a request; on completion copy its k ids / distances to host buffers
+ * (either may be NULL) and forget the ticket.  GF_ETIMEOUT if it has not finished by then (the
+ * ticket stays valid); the request's own error code if its batch failed. */
+int gf_server_poll(gf_server *S, uint64_t ticket, int64_t *ids_host, float *dists_host,
+                   int32_t timeout_us);
+
+int gf_server_get_stats(gf_server *S, gf_server_stats *st);
+int gf_server_reset_stats(gf_server *S);
+
+/* Open-loop load for measurement: Poisson arrivals at rate_qps for duration_s seconds, each for a
+ * forest drawn uniformly, queries taken in turn from queries_host[f] (host [nq[f]][d_f]); waits up
+ * to timeout_ms per request, then fills st. */
+int gf_server_run_poisson(gf_server *S, const float *const *queries_host, const int64_t *nq,
+                          double rate_qps, double duration_s, int32_t k, uint64_t seed,
+                          int32_t timeout_ms, gf_server_stats *st);
+
+/* Stop the threads after the batches in flight finish, free the slots.  Pending tickets die. */
+int gf_server_destroy(gf_server *S);
 
 /* ---------------------------------------------------------------- misc */
 

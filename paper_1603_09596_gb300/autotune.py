@@ -1,0 +1,73 @@
+"""Autotuner for the query kernel: CTA shape per precision and the screening shortlist R.
+
+For a resident forest and a sample of queries it
+  1. times every (warps per CTA, CTAs per SM) shape of the query kernel in each precision and
+     keeps the fastest;
+  2. for a screened precision, picks the shortest shortlist R whose answers agree with the
+     float32 search on at least `agree` of the sample's top-k entries (the screen only decides
+     which candidates get the exact float32 rerank, so this is what R trades away);
+and stores the choice in the forest (gf_forest_set_tuning), where gf_query picks it up.
+Results are cached per (n, d, T, leaf_size, k, precision, batch) for the process.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import gf
+
+_cache: dict = {}
+
+SHAPES = [(4, 0), (8, 0), (8, 2), (8, 3), (16, 0), (16, 1), (4, 4), (8, 4)]
+R_CHOICES = [16, 32, 64, 128, 256]
+
+
+def _time(fn, reps: int = 3) -> float:
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0.995,
+         shapes=SHAPES, r_choices=R_CHOICES) -> dict:
+    inf = F.info
+    key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0])
+    if key in _cache:
+        res = _cache[key]
+        gf.gf_forest_set_tuning(F, precision, res["warps"], res["ctas_per_sm"], res.get("R", 0))
+        return res
+    res: dict = {"precision": precision}
+    R = 0
+    if precision != gf.GF_FP32:
+        ref_ids, _ = gf.gf_query(F, Q, k)
+        R = r_choices[-1]
+        for r in r_choices:
+            if r < k:
+                continue
+            ids, _ = gf.gf_query(F, Q, k, precision=precision, rerank_R=r)
+            hit = (ids[:, :, None] == ref_ids[:, None, :]).any(-1).float().mean().item()
+            res.setdefault("agreement", {})[r] = hit
+            if hit >= agree:
+                R = r
+                break
+        res["R"] = R
+    timings = {}
+    for w, c in shapes:
+        try:
+            t = _time(lambda: gf.gf_query(F, Q, k, precision=precision, rerank_R=R, warps_per_cta=w,
+                                          ctas_per_sm=c))
+        except gf.GFError:
+            continue
+        timings[(w, c)] = t
+    (w, c), t = min(timings.items(), key=lambda kv: kv[1])
+    res.update(warps=w, ctas_per_sm=c, ms=t, timings={f"{a}x{b}": v for (a, b), v in timings.items()})
+    gf.gf_forest_set_tuning(F, precision, w, c, R)
+    _cache[key] = res
+    return res

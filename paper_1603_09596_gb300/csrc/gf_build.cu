@@ -22,6 +22,7 @@
 // (the variance partial sums of the chunks are added in a fixed order, so the build is
 // deterministic); deeper levels use one CTA per node that keeps the node's keys in shared memory.
 #include "gf_internal.cuh"
+#include "gf_device.cuh"
 
 #include <algorithm>
 #include <utility>
@@ -29,13 +30,14 @@
 
 namespace {
 
+using namespace gfdev;
+
 constexpr int NT = 256;        // threads per CTA in every build kernel
 constexpr int DPT = 4;         // dimensions per thread per dimension block
 constexpr int DB = NT * DPT;   // dimensions per block
 constexpr int CHUNK = 2048;    // points per chunk on the chunked levels
 constexpr int SMALL = 8192;    // nodes up to this size are built by one CTA
 constexpr int TMAX = 64;       // largest supported t
-constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------- random numbers
 // SplitMix64 (Steele, Lea, Flood 2014) output number i of the stream starting at s0, and the
@@ -207,68 +209,6 @@ __device__ void topt_merge(const double *vblk, int nb, int dbase, double *topv, 
 __device__ __forceinline__ int pick_dim(const BuildParams &P, unsigned long long tk, int j, const int *D) {
     const unsigned long long u = sm64_at(tk, (unsigned long long)j + 1ull);
     return D[u % (unsigned long long)P.t];
-}
-
-// ---------------------------------------------------------------- block radix select
-
-// Aggregated shared-memory histogram increment (lanes with equal bins add once).
-__device__ __forceinline__ void hist_add(unsigned *hist, unsigned bin, bool active) {
-    const unsigned mask = __ballot_sync(FULL, active);
-    if (!active) return;
-    const unsigned peers = __match_any_sync(mask, bin);
-    if ((threadIdx.x & 31) == (__ffs(peers) - 1)) atomicAdd(hist + bin, __popc(peers));
-}
-
-// Rank-h key (0-based) among keys[0..cnt) held in shared memory; keys are distinct.
-__device__ unsigned long long block_select(const unsigned long long *keys, int cnt, int h, unsigned *hist,
-                                           unsigned long long *sh_pref, int *sh_h) {
-    if (threadIdx.x == 0) { *sh_pref = 0ull; *sh_h = h; }
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 56 - 8 * pass;
-        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
-        __syncthreads();
-        const unsigned long long pref = *sh_pref;
-        const int iters = (cnt + blockDim.x - 1) / blockDim.x;
-        for (int it = 0; it < iters; ++it) {
-            const int i = it * blockDim.x + threadIdx.x;
-            bool act = false;
-            unsigned bin = 0;
-            if (i < cnt) {
-                const unsigned long long k = keys[i];
-                act = pass == 0 || ((k ^ pref) >> (shift + 8)) == 0ull;
-                bin = (unsigned)(k >> shift) & 255u;
-            }
-            hist_add(hist, bin, act);
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            // lane owns bins 8*lane .. 8*lane+7
-            unsigned c[8], s = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) { c[q] = hist[8 * lane + q]; s += c[q]; }
-            unsigned incl = s;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned v = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const unsigned before = incl - s;
-            const unsigned hr = (unsigned)*sh_h;
-            if (hr >= before && hr < incl) {
-                unsigned acc = before;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (hr >= acc && hr < acc + c[q]) {
-                        *sh_pref = pref | ((unsigned long long)(8 * lane + q) << shift);
-                        *sh_h = (int)(hr - acc);
-                    }
-                    acc += c[q];
-                }
-            }
-        }
-        __syncthreads();
-    }
-    return *sh_pref;
 }
 
 // Stable partition of rows[0..cnt) by key < kh into out[0..h) and out[h..cnt).

@@ -317,7 +317,33 @@ extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_
     const int warps = o->warps_per_cta > 0 ? o->warps_per_cta : F->tune_warps[p];
     if (warps > 32) return gf_fail(GF_EINVAL, "warps_per_cta=%d > 32", warps);
     const int cps = o->ctas_per_sm > 0 ? o->ctas_per_sm : F->tune_ctas[p];
-    return gf_launch_query(F, Q, m, k, p, R, warps, cps, (cudaStream_t)o->stream, ids, dists);
+    if (o->algo < GF_ALGO_AUTO || o->algo > GF_ALGO_STREAM) return gf_fail(GF_EINVAL, "unknown algo %d", o->algo);
+    QueryExtra x;
+    x.algo = o->algo;
+    x.workspace = o->workspace;
+    x.workspace_bytes = o->workspace_bytes;
+    x.ncand_out = o->ncand_out;
+    return gf_launch_query(F, Q, m, k, p, R, warps, cps, (cudaStream_t)o->stream, ids, dists, x);
+}
+
+int gf_stream_grid(const gf_forest *F, int64_t m, int warps, int ctas_per_sm, int precision, int k, int R,
+                   long long *grid);
+
+extern "C" int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_query_opts *o, int64_t *bytes) {
+    if (!F || !bytes) return gf_fail(GF_EINVAL, "null argument");
+    gf_query_opts def;
+    gf_query_opts_default(&def);
+    if (!o) o = &def;
+    const int p = o->precision;
+    if (p < 0 || p > 2) return gf_fail(GF_EINVAL, "unknown precision %d", p);
+    const int warps = o->warps_per_cta > 0 ? o->warps_per_cta : F->tune_warps[p];
+    const int cps = o->ctas_per_sm > 0 ? o->ctas_per_sm : F->tune_ctas[p];
+    const int R = o->rerank_R > 0 ? o->rerank_R : F->tune_R[p];
+    long long grid = 0;
+    int r = gf_stream_grid(F, m, warps, cps, p, 1, R, &grid);
+    if (r) return r;
+    *bytes = (int64_t)grid * ((F->n + 31) / 32) * 4;
+    return GF_OK;
 }
 
 extern "C" int gf_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int64_t *ids,

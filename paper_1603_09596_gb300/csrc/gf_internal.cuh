@@ -93,6 +93,13 @@ int gf_cuda_fail(cudaError_t e, const char *what);
 int gf_dmalloc(void **p, size_t bytes);
 
 // ---------------------------------------------------------------- entry points between units
+struct QueryExtra {
+    int32_t algo = GF_ALGO_AUTO;
+    void *workspace = nullptr;
+    int64_t workspace_bytes = 0;
+    int32_t *ncand_out = nullptr;
+};
+
 int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,
                     int32_t R, int32_t warps, int32_t ctas_per_sm, cudaStream_t s, int64_t *ids,
-                    float *dists);
+                    float *dists, const QueryExtra &x);

@@ -12,12 +12,14 @@
 // The scoring loop is the only part that touches HBM in bulk: every candidate row is streamed
 // once with 16-byte read-only loads that bypass L1, a warp per row, two rows in flight per warp.
 #include "gf_internal.cuh"
+#include "gf_device.cuh"
 
+#include <algorithm>
 #include <climits>
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
+using gfdev::FULL;
 constexpr unsigned long long KEY_NONE = ~0ull;
 
 __device__ __forceinline__ uint4 ld_u4(const void *p) {
@@ -175,79 +177,110 @@ __device__ __forceinline__ void acc_fp8w(float4 &a, const float4 q, unsigned w, 
 // Precision tags
 constexpr int P_F32 = 0, P_BF16 = 1, P_FP8 = 2;
 
+template <int PREC>
+struct Prec {
+    static constexpr int QF4 = PREC == P_F32 ? 1 : PREC == P_BF16 ? 2 : 4;  // query float4s per chunk
+};
+
+// Row pitch (bytes) and base pointer of the points in a precision; a chunk is 16 bytes.
+template <int PREC>
+__device__ __forceinline__ size_t row_pitch(const ForestView &F) {
+    return PREC == P_F32 ? (size_t)F.ldx * 4 : PREC == P_BF16 ? (size_t)F.ldb * 2 : (size_t)F.ld8;
+}
+
+template <int PREC>
+__device__ __forceinline__ const unsigned char *row_base(const ForestView &F) {
+    return PREC == P_F32 ? (const unsigned char *)F.x
+         : PREC == P_BF16 ? (const unsigned char *)F.xb : F.x8;
+}
+
+// The query values matching a lane's chunks (NC > 0: chunks lane, lane+32, ...), in registers.
+template <int PREC, int NC>
+__device__ __forceinline__ void load_qreg(const ForestView &F, const float *qs, float4 *qr) {
+    constexpr int QF4 = Prec<PREC>::QF4;
+    const int lane = threadIdx.x & 31;
+    const int nch = (int)(row_pitch<PREC>(F) >> 4);
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+#pragma unroll
+    for (int c = 0; c < (NC > 0 ? NC : 0); ++c) {
+        const int cc = lane + 32 * c;
+#pragma unroll
+        for (int h = 0; h < QF4; ++h)
+            qr[c * QF4 + h] = cc < nch ? q4[cc * QF4 + h] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Squared distances of the query to rows i0 and i1 (both valid ids), by the whole warp; every
+// lane returns both sums.  NC > 0: a lane holds at most NC 16-byte chunks of a row and the query's
+// matching values in qr; NC == 0: any row length, query read from shared memory.
+template <int PREC, int NC>
+__device__ __forceinline__ void warp_dist2(const ForestView &F, const float4 *qr, const float *qs, int i0,
+                                           int i1, float &d0, float &d1) {
+    constexpr int QF4 = Prec<PREC>::QF4;
+    const int lane = threadIdx.x & 31;
+    const size_t pitch = row_pitch<PREC>(F);
+    const int nch = (int)(pitch >> 4);
+    const unsigned char *r0 = row_base<PREC>(F) + (size_t)i0 * pitch;
+    const unsigned char *r1 = row_base<PREC>(F) + (size_t)i1 * pitch;
+    const float s0 = PREC == P_FP8 ? __ldg(F.scale8 + i0) : 0.f;
+    const float s1 = PREC == P_FP8 ? __ldg(F.scale8 + i1) : 0.f;
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+    constexpr int UB = NC > 0 ? NC : 4;  // chunks per lane loaded before use
+    for (int c0 = lane; c0 < nch; c0 += 32 * UB) {
+        uint4 x0[UB], x1[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int cc = c0 + 32 * u;
+            if (cc < nch) {
+                x0[u] = ld_u4(r0 + ((size_t)cc << 4));
+                x1[u] = ld_u4(r1 + ((size_t)cc << 4));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int cc = c0 + 32 * u;
+            if (cc < nch) {
+                float4 qa[QF4];
+#pragma unroll
+                for (int h = 0; h < QF4; ++h) qa[h] = NC > 0 ? qr[u * QF4 + h] : q4[cc * QF4 + h];
+                if (PREC == P_F32) {
+                    acc4(a0, qa[0], *reinterpret_cast<const float4 *>(&x0[u]));
+                    acc4(a1, qa[0], *reinterpret_cast<const float4 *>(&x1[u]));
+                } else if (PREC == P_BF16) {
+                    acc_bf16(a0, qa[0], qa[1], x0[u]);
+                    acc_bf16(a1, qa[0], qa[1], x1[u]);
+                } else {
+                    acc_fp8w(a0, qa[0], x0[u].x, s0); acc_fp8w(a0, qa[1], x0[u].y, s0);
+                    acc_fp8w(a0, qa[2], x0[u].z, s0); acc_fp8w(a0, qa[3], x0[u].w, s0);
+                    acc_fp8w(a1, qa[0], x1[u].x, s1); acc_fp8w(a1, qa[1], x1[u].y, s1);
+                    acc_fp8w(a1, qa[2], x1[u].z, s1); acc_fp8w(a1, qa[3], x1[u].w, s1);
+                }
+            }
+        }
+        if (NC > 0) break;  // one pass covers the row
+    }
+    d0 = warp_sum(sum4(a0));
+    d1 = warp_sum(sum4(a1));
+}
+
 // Score candidates ids[0..C) of the query in qs (float32, zero-padded to a multiple of 16) and
 // write one key per candidate.  Warp w takes rows w, w + nw, ...; two rows are in flight per
-// warp.  NC > 0: a lane holds at most NC chunks of a row (chunk = 16 bytes), with the query's
-// matching values in registers; NC == 0: any row length, query read from shared memory.
+// warp.  An id outside [0, n) gets the empty key.
 template <int PREC, int NC>
 __device__ void score_rows(const ForestView &F, const float *qs, const int *ids, int C,
                            unsigned long long *keys) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // row pitch in bytes and chunks per row
-    const size_t pitch = PREC == P_F32 ? (size_t)F.ldx * 4 : PREC == P_BF16 ? (size_t)F.ldb * 2 : (size_t)F.ld8;
-    const int nch = (int)(pitch >> 4);
-    const unsigned char *base = PREC == P_F32 ? (const unsigned char *)F.x
-                              : PREC == P_BF16 ? (const unsigned char *)F.xb : F.x8;
-    constexpr int QF4 = PREC == P_F32 ? 1 : PREC == P_BF16 ? 2 : 4;  // query float4s per chunk
-    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
-    constexpr int NR = NC > 0 ? NC : 1;
-    float4 qr[NR * QF4];
-    if (NC > 0) {
-#pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            const int cc = lane + 32 * c;
-#pragma unroll
-            for (int h = 0; h < QF4; ++h)
-                qr[c * QF4 + h] = cc < nch ? q4[cc * QF4 + h] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
+    float4 qr[(NC > 0 ? NC : 1) * Prec<PREC>::QF4];
+    load_qreg<PREC, NC>(F, qs, qr);
     for (int j = w; j < C; j += 2 * nw) {
         const int j1 = j + nw;
         const int i0 = ids[j];
         const int i1 = j1 < C ? ids[j1] : i0;
         const bool v0 = (unsigned)i0 < (unsigned long long)F.n;
         const bool v1 = (unsigned)i1 < (unsigned long long)F.n;
-        const unsigned char *r0 = base + (size_t)(v0 ? i0 : 0) * pitch;
-        const unsigned char *r1 = base + (size_t)(v1 ? i1 : 0) * pitch;
-        const float s0 = PREC == P_FP8 ? __ldg(F.scale8 + (v0 ? i0 : 0)) : 0.f;
-        const float s1 = PREC == P_FP8 ? __ldg(F.scale8 + (v1 ? i1 : 0)) : 0.f;
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-        constexpr int UB = NC > 0 ? NC : 4;  // chunks per lane loaded before use
-        for (int c0 = lane; c0 < nch; c0 += 32 * UB) {
-            uint4 x0[UB], x1[UB];
-#pragma unroll
-            for (int u = 0; u < UB; ++u) {
-                const int cc = c0 + 32 * u;
-                if (cc < nch) {
-                    x0[u] = ld_u4(r0 + ((size_t)cc << 4));
-                    x1[u] = ld_u4(r1 + ((size_t)cc << 4));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UB; ++u) {
-                const int cc = c0 + 32 * u;
-                if (cc < nch) {
-                    float4 qa[QF4];
-#pragma unroll
-                    for (int h = 0; h < QF4; ++h) qa[h] = NC > 0 ? qr[u * QF4 + h] : q4[cc * QF4 + h];
-                    if (PREC == P_F32) {
-                        acc4(a0, qa[0], *reinterpret_cast<const float4 *>(&x0[u]));
-                        acc4(a1, qa[0], *reinterpret_cast<const float4 *>(&x1[u]));
-                    } else if (PREC == P_BF16) {
-                        acc_bf16(a0, qa[0], qa[1], x0[u]);
-                        acc_bf16(a1, qa[0], qa[1], x1[u]);
-                    } else {
-                        acc_fp8w(a0, qa[0], x0[u].x, s0); acc_fp8w(a0, qa[1], x0[u].y, s0);
-                        acc_fp8w(a0, qa[2], x0[u].z, s0); acc_fp8w(a0, qa[3], x0[u].w, s0);
-                        acc_fp8w(a1, qa[0], x1[u].x, s1); acc_fp8w(a1, qa[1], x1[u].y, s1);
-                        acc_fp8w(a1, qa[2], x1[u].z, s1); acc_fp8w(a1, qa[3], x1[u].w, s1);
-                    }
-                }
-            }
-            if (NC > 0) break;  // one pass covers the row
-        }
-        const float d0 = warp_sum(sum4(a0));
-        const float d1 = warp_sum(sum4(a1));
+        float d0, d1;
+        warp_dist2<PREC, NC>(F, qr, qs, v0 ? i0 : 0, v1 ? i1 : 0, d0, d1);
         if (lane == 0) {
             keys[j] = v0 ? make_key(d0, i0) : KEY_NONE;
             if (j1 < C) keys[j1] = v1 ? make_key(d1, i1) : KEY_NONE;
@@ -435,6 +468,193 @@ __global__ void k_query_fused(ForestView F, const float *__restrict__ Q, long lo
     }
 }
 
+// ---------------------------------------------------------------- streaming path
+//
+// For candidate sets of any size.  The CTA walks the concatenated leaf ranges of its query in
+// chunks of 32 positions per warp.  A bitmap over the point ids in global memory -- one per CTA,
+// the "seen" array of Sec. 2.3 -- admits every id once (atomicOr test-and-set); admitted rows are
+// scored two at a time per warp and their keys appended to a shared buffer when they beat the
+// running threshold.  When the buffer fills, a radix select keeps the best `keep` keys and raises
+// the threshold.  At the end the kept keys are sorted (and, for a screened precision, rescored in
+// float32) and the bits the query set are cleared again, so the bitmap is all zero between queries.
+
+struct StreamLayout {
+    size_t buf, qs, pref, lofs, lcnt, lpos, hist, wtmp, sh, total;
+};
+
+__host__ __device__ inline StreamLayout stream_layout(int d, int T, int buf_len) {
+    StreamLayout L;
+    size_t o = 0;
+    L.buf = o;  o += (size_t)buf_len * 8;
+    L.qs = o;   o += (size_t)ldq_of(d) * 4;
+    L.pref = o; o += 16;  // select prefix, threshold
+    L.lofs = o; o += (size_t)T * 4;
+    L.lcnt = o; o += (size_t)T * 4;
+    L.lpos = o; o += (size_t)(T + 1) * 4;
+    L.hist = o; o += 256 * 4;
+    L.wtmp = o; o += 64 * 4;
+    L.sh = o;   o += 8 * 4;
+    L.total = o;
+    return L;
+}
+
+// largest t with lpos[t] <= pos (lpos[0] = 0 <= pos < lpos[T])
+__device__ __forceinline__ int tree_of_pos(const int *lpos, int T, int pos) {
+    int lo = 0, hi = T;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (lpos[mid] <= pos) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// In-place stable compaction of buf[0..cnt) to the keys <= kth.
+__device__ void compact_le(unsigned long long *buf, int cnt, unsigned long long kth, int *wtmp, int *run) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) *run = 0;
+    __syncthreads();
+    for (int base = 0; base < cnt; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const unsigned long long key = i < cnt ? buf[i] : KEY_NONE;
+        const bool keep = i < cnt && key <= kth;
+        const unsigned bl = __ballot_sync(FULL, keep);
+        if (lane == 0) wtmp[w] = __popc(bl);
+        __syncthreads();
+        int off = *run;
+        for (int q = 0; q < w; ++q) off += wtmp[q];
+        off += __popc(bl & ((1u << lane) - 1u));
+        if (keep) buf[off] = key;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int q = 0; q < nw; ++q) t += wtmp[q];
+            *run += t;
+        }
+        __syncthreads();
+    }
+}
+
+template <int PREC, int NC, int NCF>
+__global__ void k_query_stream(ForestView F, const float *__restrict__ Q, long long m, int k, int R,
+                               int buf_len, unsigned *bitmaps, int nwords, long long *ids, float *dists,
+                               int *ncand_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const StreamLayout Ly = stream_layout(F.d, F.T, buf_len);
+    unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem_raw + Ly.buf);
+    float *qs = reinterpret_cast<float *>(smem_raw + Ly.qs);
+    unsigned long long *pref = reinterpret_cast<unsigned long long *>(smem_raw + Ly.pref);
+    unsigned long long *thr = pref + 1;
+    int *lofs = reinterpret_cast<int *>(smem_raw + Ly.lofs);
+    int *lcnt = reinterpret_cast<int *>(smem_raw + Ly.lcnt);
+    int *lpos = reinterpret_cast<int *>(smem_raw + Ly.lpos);
+    unsigned *hist = reinterpret_cast<unsigned *>(smem_raw + Ly.hist);
+    int *wtmp = reinterpret_cast<int *>(smem_raw + Ly.wtmp);
+    int *sh = reinterpret_cast<int *>(smem_raw + Ly.sh);  // [0] scratch [1] count [2] total [3] fresh [4] select
+    int *sl = reinterpret_cast<int *>(buf + buf_len / 2);  // shortlist ids (upper half of buf)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int keep = PREC == P_F32 ? k : R;
+    const int limit = buf_len - 32 * nw;
+    unsigned *bm = bitmaps + (size_t)blockIdx.x * nwords;
+
+    for (long long qi = blockIdx.x; qi < m; qi += gridDim.x) {
+        load_query(Q + qi * F.d, F.d, qs);
+        __syncthreads();
+        for (int t = threadIdx.x; t < F.T; t += blockDim.x)
+            leaf_range(F, t, descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, qs), lofs, lcnt);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int t = 0; t < F.T; ++t) {
+                lpos[t] = acc;
+                acc += lcnt[t];
+            }
+            lpos[F.T] = acc;
+            sh[1] = 0;
+            sh[2] = acc;
+            sh[3] = 0;
+            *thr = KEY_NONE;
+        }
+        __syncthreads();
+        const int tot = sh[2];
+        float4 qr[(NC > 0 ? NC : 1) * Prec<PREC>::QF4];
+        load_qreg<PREC, NC>(F, qs, qr);
+        const int nchunk = (tot + 31) >> 5;
+        for (int c0 = 0; c0 < nchunk; c0 += nw) {
+            const int c = c0 + w;
+            if (c < nchunk) {
+                const int pos = (c << 5) + lane;
+                int id = -1;
+                if (pos < tot) {
+                    const int t = tree_of_pos(lpos, F.T, pos);
+                    id = __ldg(F.perm + (size_t)t * F.n + lofs[t] + (pos - lpos[t]));
+                }
+                bool fresh = false;
+                if (id >= 0) {
+                    const unsigned bit = 1u << (id & 31);
+                    fresh = !(atomicOr(bm + (id >> 5), bit) & bit);
+                }
+                unsigned mask = __ballot_sync(FULL, fresh);
+                if (lane == 0 && mask) atomicAdd(&sh[3], __popc(mask));
+                while (mask) {
+                    const int b0 = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const bool two = mask != 0;
+                    const int b1 = two ? __ffs(mask) - 1 : b0;
+                    if (two) mask &= mask - 1;
+                    const int i0 = __shfl_sync(FULL, id, b0);
+                    const int i1 = __shfl_sync(FULL, id, b1);
+                    float d0, d1;
+                    warp_dist2<PREC, NC>(F, qr, qs, i0, i1, d0, d1);
+                    if (lane == 0) {
+                        const unsigned long long th = *reinterpret_cast<volatile unsigned long long *>(thr);
+                        const unsigned long long k0 = make_key(d0, i0);
+                        if (k0 < th) buf[atomicAdd(&sh[1], 1)] = k0;
+                        if (two) {
+                            const unsigned long long k1 = make_key(d1, i1);
+                            if (k1 < th) buf[atomicAdd(&sh[1], 1)] = k1;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const int cnt_now = sh[1];
+            __syncthreads();  // every thread has read the count before any appends again
+            if (cnt_now > limit) {
+                const unsigned long long kth = gfdev::block_select(buf, cnt_now, keep - 1, hist, pref, &sh[4]);
+                compact_le(buf, cnt_now, kth, wtmp, &sh[0]);
+                if (threadIdx.x == 0) {
+                    sh[1] = keep;
+                    *thr = kth;
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        int cnt = sh[1];
+        __syncthreads();
+        if (cnt > keep) {
+            const unsigned long long kth = gfdev::block_select(buf, cnt, keep - 1, hist, pref, &sh[4]);
+            compact_le(buf, cnt, kth, wtmp, &sh[0]);
+            cnt = keep;
+        }
+        sort_keys(buf, cnt);
+        if (PREC != P_F32) {
+            for (int j = threadIdx.x; j < cnt; j += blockDim.x) sl[j] = (int)(unsigned)(buf[j] & 0xffffffffu);
+            __syncthreads();
+            score_rows<P_F32, NCF>(F, qs, sl, cnt, buf);
+            sort_keys(buf, cnt);
+        }
+        write_topk(buf, cnt, k, ids + qi * k, dists + qi * k);
+        for (int pos = threadIdx.x; pos < tot; pos += blockDim.x) {
+            const int t = tree_of_pos(lpos, F.T, pos);
+            bm[__ldg(F.perm + (size_t)t * F.n + lofs[t] + (pos - lpos[t])) >> 5] = 0u;
+        }
+        if (threadIdx.x == 0 && ncand_out) ncand_out[qi] = sh[3];
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 int nc_for(int chunks) {
@@ -491,14 +711,100 @@ int launch_fused(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32
     return GF_OK;
 }
 
+int stream_buf_len(int keep, int warps) {
+    int kp = 1;
+    while (kp < keep) kp <<= 1;
+    return next_pow2(std::max(2048, 2 * (kp + 32 * warps)));
+}
+
+template <int PREC, int NC, int NCF>
+int launch_stream(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
+                  int ctas_per_sm, cudaStream_t st, int64_t *ids, float *dists, const QueryExtra &x,
+                  long long *grid_only = nullptr) {
+    const int keep = PREC == P_F32 ? k : R;
+    const int buf_len = stream_buf_len(keep, warps);
+    const size_t smem = stream_layout(F->d, F->T, buf_len).total;
+    int r = check_smem(F, smem);
+    if (r) return r;
+    auto kern = k_query_stream<PREC, NC, NCF>;
+    if ((r = prep_kernel(kern, smem))) return r;
+    const int threads = warps * 32;
+    cudaFuncAttributes fa;
+    GF_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    if (threads > fa.maxThreadsPerBlock)
+        return gf_fail(GF_EINVAL, "warps_per_cta=%d exceeds this kernel's limit of %d threads (%d registers)",
+                       warps, fa.maxThreadsPerBlock, fa.numRegs);
+    if (ctas_per_sm <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+        ctas_per_sm = occ > 0 ? occ : 1;
+    }
+    long long grid = (long long)F->num_sms * ctas_per_sm;
+    if (grid > m) grid = m;
+    if (grid_only) {
+        *grid_only = grid;
+        return GF_OK;
+    }
+    const int nwords = (int)((F->n + 31) / 32);
+    const size_t ws_bytes = (size_t)grid * nwords * 4;
+    unsigned *bitmaps = (unsigned *)x.workspace;
+    bool own = false;
+    if (bitmaps) {
+        if ((size_t)x.workspace_bytes < ws_bytes)
+            return gf_fail(GF_EINVAL, "workspace of %lld bytes, %zu needed", (long long)x.workspace_bytes, ws_bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync((void **)&bitmaps, ws_bytes, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return gf_fail(GF_ENOMEM, "query workspace of %zu bytes: %s", ws_bytes, cudaGetErrorString(e));
+        }
+        own = true;
+        e = cudaMemsetAsync(bitmaps, 0, ws_bytes, st);
+        if (e != cudaSuccess) { cudaFreeAsync(bitmaps, st); return gf_cuda_fail(e, "workspace memset"); }
+    }
+    kern<<<(unsigned)grid, threads, smem, st>>>(view_of(F), Q, m, k, R, buf_len, bitmaps, nwords,
+                                               (long long *)ids, dists, x.ncand_out);
+    cudaError_t e = cudaGetLastError();
+    if (own) cudaFreeAsync(bitmaps, st);
+    if (e != cudaSuccess) return gf_cuda_fail(e, "k_query_stream launch");
+    return GF_OK;
+}
+
 template <int PREC>
-int dispatch_prec(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
-                  int cps, cudaStream_t st, int64_t *ids, float *dists) {
+int stream_grid_prec(const gf_forest *F, int64_t m, int k, int R, int warps, int cps, long long *grid) {
     const int chunks = PREC == P_F32 ? F->ldx / 4 : PREC == P_BF16 ? F->ldb / 8 : F->ld8 / 16;
     const int ncf = nc_for(F->ldx / 4);
     const int nc = nc_for(chunks);
-#define GF_CASE(A, B)                                                                       \
-    if (nc == A && ncf == B) return launch_fused<PREC, A, B>(F, Q, m, k, R, warps, cps, st, ids, dists);
+    QueryExtra x;
+#define GF_G(A, B) \
+    if (nc == A && ncf == B) return launch_stream<PREC, A, B>(F, nullptr, m, k, R, warps, cps, 0, nullptr, nullptr, x, grid);
+    if (PREC == P_F32) {
+        GF_G(1, 1) GF_G(2, 2) GF_G(4, 4) GF_G(8, 8) GF_G(0, 0)
+    } else {
+        GF_G(1, 1) GF_G(1, 2) GF_G(1, 4) GF_G(2, 4) GF_G(2, 8) GF_G(4, 8)
+        GF_G(1, 8) GF_G(4, 0) GF_G(8, 0) GF_G(0, 0) GF_G(2, 0) GF_G(1, 0)
+    }
+#undef GF_G
+    return gf_fail(GF_EUNSUPPORTED, "no kernel for chunk classes %d/%d", nc, ncf);
+}
+
+template <int PREC>
+int dispatch_prec(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
+                  int cps, cudaStream_t st, int64_t *ids, float *dists, const QueryExtra &x) {
+    const int chunks = PREC == P_F32 ? F->ldx / 4 : PREC == P_BF16 ? F->ldb / 8 : F->ld8 / 16;
+    const int ncf = nc_for(F->ldx / 4);
+    const int nc = nc_for(chunks);
+    int algo = x.algo;
+    if (algo == GF_ALGO_AUTO) {
+        const size_t sort_smem = smem_bytes(F->d, F->T, F->cand_cap);
+        algo = (F->cand_cap <= 4096 && sort_smem <= 100 * 1024 && !x.ncand_out) ? GF_ALGO_SORT : GF_ALGO_STREAM;
+    }
+    if (algo == GF_ALGO_SORT && x.ncand_out)
+        return gf_fail(GF_EINVAL, "candidate counts are reported by the streaming kernel only");
+#define GF_CASE(A, B)                                                                              \
+    if (nc == A && ncf == B)                                                                       \
+        return algo == GF_ALGO_SORT ? launch_fused<PREC, A, B>(F, Q, m, k, R, warps, cps, st, ids, dists) \
+                                    : launch_stream<PREC, A, B>(F, Q, m, k, R, warps, cps, st, ids, dists, x);
     if (PREC == P_F32) {
         GF_CASE(1, 1) GF_CASE(2, 2) GF_CASE(4, 4) GF_CASE(8, 8) GF_CASE(0, 0)
     } else {
@@ -514,11 +820,21 @@ int dispatch_prec(const gf_forest *F, const float *Q, int64_t m, int32_t k, int3
 
 int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,
                     int32_t R, int32_t warps, int32_t ctas_per_sm, cudaStream_t st, int64_t *ids,
-                    float *dists) {
+                    float *dists, const QueryExtra &x) {
     switch (precision) {
-        case GF_FP32: return dispatch_prec<P_F32>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists);
-        case GF_BF16_RERANK: return dispatch_prec<P_BF16>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists);
-        case GF_FP8_RERANK: return dispatch_prec<P_FP8>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists);
+        case GF_FP32: return dispatch_prec<P_F32>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x);
+        case GF_BF16_RERANK: return dispatch_prec<P_BF16>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x);
+        case GF_FP8_RERANK: return dispatch_prec<P_FP8>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x);
+    }
+    return gf_fail(GF_EINVAL, "unknown precision %d", precision);
+}
+
+int gf_stream_grid(const gf_forest *F, int64_t m, int warps, int ctas_per_sm, int precision, int k, int R,
+                   long long *grid) {
+    switch (precision) {
+        case GF_FP32: return stream_grid_prec<P_F32>(F, m, k, R, warps, ctas_per_sm, grid);
+        case GF_BF16_RERANK: return stream_grid_prec<P_BF16>(F, m, k, R, warps, ctas_per_sm, grid);
+        case GF_FP8_RERANK: return stream_grid_prec<P_FP8>(F, m, k, R, warps, ctas_per_sm, grid);
     }
     return gf_fail(GF_EINVAL, "unknown precision %d", precision);
 }

@@ -31,9 +31,30 @@ class RandParams(C.Structure):
                 ("householder", C.c_int32)]
 
 
+GF_ALGO_AUTO, GF_ALGO_SORT, GF_ALGO_STREAM = 0, 1, 2
+
+
 class QueryOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rerank_R", C.c_int32), ("warps_per_cta", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("stream", C.c_void_p)]
+                ("ctas_per_sm", C.c_int32), ("stream", C.c_void_p), ("algo", C.c_int32),
+                ("reserved", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64),
+                ("ncand_out", C.c_void_p)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("slots", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("k_max", C.c_int32), ("precision", C.c_int32), ("rerank_R", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("batches", C.c_int64), ("mean_batch", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("span_s", C.c_double), ("qps", C.c_double), ("slots", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class ForestInfo(C.Structure):
@@ -63,10 +84,20 @@ def lib() -> C.CDLL:
             "gf_forest_free": ([P], i32),
             "gf_query": ([P, P, i64, i32, P, P], i32),
             "gf_query_ex": ([P, P, i64, i32, P, P, P], i32),
+            "gf_query_workspace_size": ([P, i64, P, P], i32),
             "gf_descend": ([P, P, i64, P, P], i32),
             "gf_candidates": ([P, P, i64, P, P, P], i32),
             "gf_score_topk": ([P, P, i64, P, P, i32, i32, P, P, P], i32),
             "gf_score_screened": ([P, P, i64, P, P, i32, i32, P, P], i32),
+            "gf_server_opts_default": ([P], None),
+            "gf_server_create": ([P, i32, P, P], i32),
+            "gf_server_slots": ([P], i32),
+            "gf_server_submit": ([P, i32, P, i32, P], i32),
+            "gf_server_poll": ([P, u64, P, P, i32], i32),
+            "gf_server_get_stats": ([P, P], i32),
+            "gf_server_reset_stats": ([P], i32),
+            "gf_server_run_poisson": ([P, P, P, C.c_double, C.c_double, i32, u64, i32, P], i32),
+            "gf_server_destroy": ([P], i32),
             "gf_last_error": ([], C.c_char_p),
             "gf_version": ([], i32),
             "gf_rand_params_default": ([P], None),
@@ -179,8 +210,19 @@ def gf_forest_set_tuning(F: Forest, precision: int, warps_per_cta: int, ctas_per
     _check(lib().gf_forest_set_tuning(F.handle, precision, warps_per_cta, ctas_per_sm, rerank_R))
 
 
+def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out):
+    o = QueryOpts(precision, rerank_R, warps_per_cta, ctas_per_sm, _stream(stream), algo, 0, None, 0, None)
+    if workspace is not None:
+        o.workspace = _dptr(workspace, workspace.dtype, "workspace")
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    if ncand_out is not None:
+        o.ncand_out = _dptr(ncand_out, torch.int32, "ncand_out")
+    return o
+
+
 def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, rerank_R: int = 0,
-             warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None,
+             warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None, algo: int = GF_ALGO_AUTO,
+             workspace: torch.Tensor | None = None, ncand_out: torch.Tensor | None = None,
              out: tuple[torch.Tensor, torch.Tensor] | None = None):
     """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k])."""
     m = Q.shape[0]
@@ -189,10 +231,18 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
         dists = torch.empty((m, k), dtype=torch.float32, device=Q.device)
     else:
         ids, dists = out
-    o = QueryOpts(precision, rerank_R, warps_per_cta, ctas_per_sm, _stream(stream))
+    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out)
     _check(lib().gf_query_ex(F.handle, _dptr(Q, torch.float32, "Q"), m, k, C.byref(o),
                              _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists")))
     return ids, dists
+
+
+def gf_query_workspace_size(F: Forest, m: int, precision: int = GF_FP32, rerank_R: int = 0,
+                            warps_per_cta: int = 0, ctas_per_sm: int = 0) -> int:
+    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, None, GF_ALGO_STREAM, None, None)
+    b = C.c_int64()
+    _check(lib().gf_query_workspace_size(F.handle, m, C.byref(o), C.byref(b)))
+    return b.value
 
 
 def gf_descend(F: Forest, Q: torch.Tensor, stream=None) -> torch.Tensor:
@@ -235,6 +285,69 @@ def gf_score_screened(F: Forest, Q: torch.Tensor, cand: torch.Tensor, ncand: tor
                                    cand.shape[1], precision, _dptr(dist, torch.float32, "dist"),
                                    _stream(stream)))
     return dist
+
+
+class Server:
+    """Continuous-batching request loop over resident forests (gf_server_* in the C ABI)."""
+
+    def __init__(self, forests, max_batch: int = 1024, slots: int = 4, hbm_budget_bytes: int = 4 << 30,
+                 k_max: int = 10, precision: int = GF_FP32, rerank_R: int = 0):
+        self.forests = list(forests)      # keep the forests alive while the server runs
+        arr = (C.c_void_p * len(self.forests))(*[f.handle for f in self.forests])
+        o = ServerOpts(max_batch, slots, hbm_budget_bytes, k_max, precision, rerank_R, 0)
+        self.handle = C.c_void_p()
+        _check(lib().gf_server_create(arr, len(self.forests), C.byref(o), C.byref(self.handle)))
+        self.dims = [f.info.d for f in self.forests]
+
+    @property
+    def slots(self) -> int:
+        return lib().gf_server_slots(self.handle)
+
+    def submit(self, forest: int, q, k: int) -> int:
+        import numpy as np
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        if q.shape != (self.dims[forest],):
+            raise ValueError("query has the wrong length")
+        t = C.c_uint64()
+        _check(lib().gf_server_submit(self.handle, forest, q.ctypes.data, k, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, k: int, timeout_us: int = 10_000_000):
+        import numpy as np
+        ids = np.empty(k, dtype=np.int64)
+        d = np.empty(k, dtype=np.float32)
+        _check(lib().gf_server_poll(self.handle, ticket, ids.ctypes.data, d.ctypes.data, timeout_us))
+        return ids, d
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().gf_server_get_stats(self.handle, C.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self) -> None:
+        _check(lib().gf_server_reset_stats(self.handle))
+
+    def run_poisson(self, queries, rate_qps: float, duration_s: float, k: int, seed: int = 0,
+                    timeout_ms: int = 60_000) -> dict:
+        import numpy as np
+        qs = [np.ascontiguousarray(q, dtype=np.float32) for q in queries]
+        ptrs = (C.c_void_p * len(qs))(*[q.ctypes.data for q in qs])
+        nq = (C.c_int64 * len(qs))(*[q.shape[0] for q in qs])
+        st = ServerStats()
+        _check(lib().gf_server_run_poisson(self.handle, ptrs, nq, rate_qps, duration_s, k, seed,
+                                           timeout_ms, C.byref(st)))
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self.handle:
+            _check(lib().gf_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gf_version() -> int:

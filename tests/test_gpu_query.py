@@ -237,3 +237,85 @@ def test_screened_distances_elementwise(gf, prec, name):
         c = cand[i, :nc[i]]
         ref = ((deq[c] - Q[i].astype(np.float64)) ** 2).sum(axis=1)
         np.testing.assert_allclose(dist[i, :nc[i]], ref, rtol=RTOL, atol=RTOL * ref.max())
+
+
+# ---------------------------------------------------------------- streaming kernel (bitmap dedupe)
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("k", [1, 10])
+def test_stream_matches_oracle_and_counts(gf, name, k):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    nc = torch.full((Q.shape[0],), -1, dtype=torch.int32, device="cuda")
+    gi, gd = gf.gf_query(G, Qg, k, algo=gf.GF_ALGO_STREAM, ncand_out=nc)
+    oi, od, onc = oracle.search(F, X, Q, k, return_ncand=True)
+    assert np.array_equal(nc.cpu().numpy(), onc)        # the bitmap admits each candidate once
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("name", ["tiny", "ragged", "gist_like"])
+def test_stream_equals_sort_kernel(gf, prec, name):
+    # same row arithmetic in both kernels: bit-identical ids and distances
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    p = gf.PRECISIONS[prec]
+    if p:
+        gf.gf_forest_add_screen(G, p)
+    Qg = torch.from_numpy(Q).cuda()
+    a = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_SORT)
+    b = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_STREAM)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_stream_caller_workspace_is_left_zero(gf):
+    X, Q, F = case("tiny")
+    G, _ = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    nbytes = gf.gf_query_workspace_size(G, Q.shape[0], ctas_per_sm=2)
+    ws = torch.zeros(nbytes // 4, dtype=torch.int32, device="cuda")
+    ref = gf.gf_query(G, Qg, 5, algo=gf.GF_ALGO_STREAM, ctas_per_sm=2)
+    for _ in range(2):
+        got = gf.gf_query(G, Qg, 5, algo=gf.GF_ALGO_STREAM, ctas_per_sm=2, workspace=ws)
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+        assert int(torch.count_nonzero(ws)) == 0
+    with pytest.raises(gf.GFError):
+        gf.gf_query(G, Qg, 5, algo=gf.GF_ALGO_STREAM, ctas_per_sm=2, workspace=ws[:10])
+
+
+_big = {}
+
+
+def big_case():
+    # leaves of 782 points in 16 trees: up to 12.5k candidates per query, beyond the sort kernel
+    if not _big:
+        X, Q = synth.mixture(50_000, 64, 60, "B", seed=5, qseed=6)
+        F = oracle.build_forest(X, 16, 1000, seed=2)
+        _big["c"] = (X, Q, F)
+    return _big["c"]
+
+
+@pytest.mark.parametrize("k", [1, 10, 300])
+def test_stream_large_candidate_sets(gf, k):
+    # k = 300 keeps a large best set, so the shared buffer is cut back many times per query
+    X, Q, F = big_case()
+    G, _ = gpu_forest(gf, X, F)
+    assert G.info.cand_cap > 4096
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k)
+    oi, od = oracle.search(F, X, Q, k)
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("R", [16, 256])
+def test_stream_large_screened(gf, prec, R):
+    X, Q, F = big_case()
+    G, _ = gpu_forest(gf, X, F)
+    gf.gf_forest_add_screen(G, gf.PRECISIONS[prec])
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, precision=gf.PRECISIONS[prec], rerank_R=R)
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    oi, od, _ = screen.screened_search(F, X, Q, 10, R, prec, offs, ids)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
