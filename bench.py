@@ -156,23 +156,47 @@ def ours(args):
     ei, ed = exact_nn(torch, Xg, Qg[:S], k)
 
     def time_query(F, prec, steps, warmup):
+        """Time `steps` launches of the batch; the launch is captured once in a CUDA graph (with a
+        caller workspace, so nothing allocates inside the capture) and replayed per step."""
         ids = torch.empty((m, k), dtype=torch.int64, device=dev)
         dd = torch.empty((m, k), dtype=torch.float32, device=dev)
-        for _ in range(warmup):
-            gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd))
+        ws = torch.zeros(gf.gf_query_workspace_size(F, m, precision=prec) // 4 + 1, dtype=torch.int32, device=dev)
+        s = torch.cuda.Stream(device=dev)
+
+        def launch():
+            gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd), workspace=ws, stream=s)
+
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                launch()
         torch.cuda.synchronize()
+        graph = None
+        if not args.no_graph:
+            try:
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=s):
+                    launch()
+                torch.cuda.synchronize()
+                with torch.cuda.stream(s):
+                    graph.replay()
+                torch.cuda.synchronize()
+            except Exception as e:  # capture not possible here: time direct launches
+                print(f"cuda graph capture failed, timing direct launches: {e}", file=sys.stderr)
+                graph = None
+                torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         with Clocks(local) as ck:
             torch.cuda.synchronize()
-            for a, b in evs:
-                a.record(stream)
-                gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd))
-                b.record(stream)
+            with torch.cuda.stream(s):
+                for a, b in evs:
+                    a.record(s)
+                    graph.replay() if graph is not None else launch()
+                    b.record(s)
             torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in evs]
-        return ids, dd, ms, ck.summary()
+        return ids, dd, ms, dict(ck.summary(), launch="cuda_graph" if graph is not None else "direct")
 
     def bytes_per_query(F, prec, C, R):
         inf = F.info
@@ -202,6 +226,7 @@ def ours(args):
             entry[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4),
                            "ms_min": round(min(ms), 4), "recall_at_1": r1, "recall_at_10": rk, "clocks": ck,
                            "R": R, "warps_per_cta": tr["warps"], "ctas_per_sm": tr["ctas_per_sm"],
+                           "rows_in_flight": tr["rows_in_flight"],
                            "bytes_per_query": round(bpq),
                            "achieved_gbs": round(bpq * m / (mean_ms / 1e3) / 1e9, 1)}
         return F, entry
@@ -253,6 +278,20 @@ def ours(args):
     e2e = {"value": round(world * m / (e_ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": m * d * 4,
            "d2h_bytes_per_step": m * k * 12}
 
+    # latency under load: single-query requests to the headline forest, Poisson arrivals at half
+    # the measured batch throughput, continuous batching (up to 1024 per batch, 4 slots)
+    lat = None
+    if not args.no_serve:
+        S = gf.Server([Fh], max_batch=1024, slots=4, hbm_budget_bytes=8 << 30, k_max=k,
+                      precision=gf.GF_BF16_RERANK, rerank_R=best["R"])
+        rate = 0.5 * value / world
+        S.run_poisson([Q[:4096]], rate_qps=min(rate, 5000), duration_s=0.3, k=k, seed=3)
+        st = S.run_poisson([Q], rate_qps=rate, duration_s=args.serve_seconds, k=k, seed=4)
+        lat = {"offered_qps": round(rate, 1), "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
+               "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 1),
+               "completed": st["completed"]}
+        S.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(X, Q, Fh, gf, k, budget_s=args.cpu_budget)
@@ -277,7 +316,8 @@ def ours(args):
         "headline_forest": {kk: head[kk] for kk in ("T", "leaf_size", "L", "build_s", "cand_per_query")},
         "at_T32_p64": spec,
         "gen_s": round(gen_s, 2),
-        "p99_ms": None,
+        "serving": lat,
+        "p99_ms": lat["p99_ms"] if lat else None,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -313,7 +353,7 @@ def profile(args):
     if prec:
         gf.gf_forest_add_screen(F, prec)
     kw = dict(precision=prec, rerank_R=args.profile_R, warps_per_cta=args.profile_warps,
-              ctas_per_sm=args.profile_ctas, algo=gf.GF_ALGO_STREAM)
+              ctas_per_sm=args.profile_ctas, algo=gf.GF_ALGO_STREAM, rows_in_flight=args.profile_rows)
     gf.gf_query(F, Qg, 10, **kw)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -325,6 +365,45 @@ def profile(args):
     print(json.dumps({"profile": True, "n": args.n, "d": args.d, "m": args.m, "T": args.T,
                       "leaf_size": args.leaf_size, "precision": args.precision,
                       "ms_per_launch": a.elapsed_time(b) / args.steps}))
+
+
+SERVE_FORESTS = [  # (n, d, T, leaf_size): six resident forests of uneven size
+    (10_000, 128, 16, 256), (50_000, 512, 16, 256), (100_000, 960, 24, 256),
+    (500_000, 960, 32, 512), (1_000_000, 960, 32, 1024), (100_000, 4096, 16, 256)]
+SERVE_RATES = [5_000, 20_000, 50_000, 100_000, 200_000]
+
+
+def serve(args):
+    """Continuous batching over six resident forests under Poisson load (k=10)."""
+    import torch
+    import paper_1603_09596_gb300 as gf
+    import synth
+    forests, queries = [], []
+    t0 = time.time()
+    for i, (n, d, T, p) in enumerate(SERVE_FORESTS):
+        X, Q = synth.mixture(n, d, 2048, "B", seed=100 + i, qseed=200 + i)
+        F = gf.gf_build(torch.from_numpy(X).cuda(), T, p, seed=i)
+        if args.precision != "fp32":
+            gf.gf_forest_add_screen(F, gf.PRECISIONS[args.precision])
+        forests.append(F)
+        queries.append(Q)
+        del X
+    setup_s = time.time() - t0
+    S = gf.Server(forests, max_batch=1024, slots=args.serve_slots, hbm_budget_bytes=args.serve_budget << 30,
+                  k_max=10, precision=gf.PRECISIONS[args.precision], rerank_R=32)
+    S.run_poisson(queries, rate_qps=5000, duration_s=0.3, k=10, seed=1)  # warm-up
+    out = []
+    for rate in SERVE_RATES:
+        st = S.run_poisson(queries, rate_qps=rate, duration_s=args.serve_seconds, k=10, seed=rate)
+        out.append({"offered_qps": rate, "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
+                    "p99_ms": round(st["p99_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                    "mean_batch": round(st["mean_batch"], 1), "completed": st["completed"]})
+    line = {"metric": "serving: q/s and p50/p99 latency, 6 resident forests, Poisson arrivals, k=10",
+            "unit": "queries/s", "precision": args.precision, "slots": S.slots,
+            "forests": [dict(n=n, d=d, T=T, leaf_size=p) for n, d, T, p in SERVE_FORESTS],
+            "setup_s": round(setup_s, 1), "rates": out}
+    S.close()
+    print(json.dumps(line))
 
 
 def reference(args):
@@ -379,17 +458,26 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--skip-spec", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--tune-sample", type=int, default=2000)
     ap.add_argument("--profile", action="store_true", help="fixed query launches for ncu")
     ap.add_argument("--T", type=int, default=HEADLINE["T"])
     ap.add_argument("--leaf-size", type=int, default=HEADLINE["leaf_size"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--profile-R", type=int, default=16)
-    ap.add_argument("--profile-warps", type=int, default=4)
+    ap.add_argument("--profile-warps", type=int, default=8)
+    ap.add_argument("--profile-rows", type=int, default=0)
     ap.add_argument("--profile-ctas", type=int, default=0)
+    ap.add_argument("--serve", action="store_true", help="serving workload (six forests, Poisson load)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget", type=int, default=8, help="GiB for batch slots")
     args = ap.parse_args()
     if args.profile:
         profile(args)
+    elif args.serve:
+        serve(args)
     elif args.impl == "reference":
         reference(args)
     else:

@@ -75,7 +75,7 @@ typedef struct gf_query_opts {
     int32_t ctas_per_sm;     /* kernel shape; 0 = forest default, else occupancy limit */
     void *stream;            /* cudaStream_t */
     int32_t algo;            /* GF_ALGO_* */
-    int32_t reserved;
+    int32_t rows_in_flight;  /* STREAM only: rows each warp scores at once, 2 or 4; 0 = default */
     void *workspace;         /* STREAM only: device scratch of at least gf_query_workspace_size()
                                 bytes, zero-filled before its first use (every query leaves it zero
                                 again); NULL = the library allocates it stream-ordered
@@ -155,9 +155,11 @@ int gf_forest_get_info(const gf_forest *F, gf_forest_info *info);
  */
 int gf_forest_add_screen(gf_forest *F, int32_t precision, void *stream);
 
-/* Set the forest's default kernel shape and shortlist (what gf_autotune writes). */
+/* Set the forest's default kernel shape and shortlist for one precision (what the autotuner
+ * writes); gf_query_ex uses them where its options hold 0.  rerank_R / rows_in_flight 0 keep the
+ * current value. */
 int gf_forest_set_tuning(gf_forest *F, int32_t precision, int32_t warps_per_cta,
-                         int32_t ctas_per_sm, int32_t rerank_R);
+                         int32_t ctas_per_sm, int32_t rerank_R, int32_t rows_in_flight);
 
 int gf_forest_free(gf_forest *F);
 

@@ -57,6 +57,9 @@ def lib():
         L.gfo_search.argtypes = [P, i64, i32, P, P, P, i32, i32, P, i64, i32, P, P, P]
         L.gfo_search.restype = None
         L.gfo_bruteforce.argtypes = [P, i64, i32, P, i64, i32, P, P]; L.gfo_bruteforce.restype = None
+        L.gfo_search_priority.argtypes = [P, i64, i32, P, P, P, i32, i32, P, i64, i32, i64, C.c_double,
+                                          P, P, P, P]
+        L.gfo_search_priority.restype = None
         L.gfo_num_threads.argtypes = []; L.gfo_num_threads.restype = i32
         _lib = L
     return _lib
@@ -197,6 +200,21 @@ def search(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, return_ncand: bool =
                      _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
                      F.L, F.T, _p(Q), m, k, _p(oi), _p(od), _p(nc))
     return (oi, od, nc) if return_ncand else (oi, od)
+
+
+def search_priority(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, c: int, eps: float = 0.0):
+    """Alg. 2 with the shared priority queue: at least the T first leaves, then leaves in order of
+    |q_s - v| until c / (1 + eps) were checked.  Returns ids, dists, candidates, leaves checked."""
+    X, Q = _f32(X), _f32(Q)
+    m = Q.shape[0]
+    oi = np.empty((m, k), dtype=np.int64)
+    od = np.empty((m, k), dtype=np.float64)
+    nc = np.empty(m, dtype=np.int64)
+    nl = np.empty(m, dtype=np.int64)
+    lib().gfo_search_priority(_p(X), F.n, F.d, _p(np.ascontiguousarray(F.split_dim)),
+                              _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
+                              F.L, F.T, _p(Q), m, k, c, eps, _p(oi), _p(od), _p(nc), _p(nl))
+    return oi, od, nc, nl
 
 
 def bruteforce(X: np.ndarray, Q: np.ndarray, k: int):

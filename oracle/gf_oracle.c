@@ -423,6 +423,139 @@ void gfo_search(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
     }
 }
 
+/* ------------------------------------------------------------------ Alg. 2 priority search */
+
+/*
+ * Alg. 2 with the shared min-priority queue Q over all trees (Sec. 2.3).  Each descent from a node
+ * to a leaf pushes, at every internal node passed, the child not taken with key |q_s - v| (Eq. 1);
+ * the leaf reached is checked: its points not seen before get their distance and enter the
+ * k-best list H.  Reading R8: the first descent of every tree checks its leaf too and counts as a
+ * checked leaf (with c = T the search is exactly R7); afterwards nodes are extracted from Q in
+ * order of (key, tree, node) and descended while fewer than c / (1 + eps) leaves were checked.
+ */
+typedef struct {
+    double key;
+    int32_t tree;
+    int64_t node;
+} qent_t;
+
+static int qent_less(const qent_t *a, const qent_t *b) {
+    if (a->key != b->key) return a->key < b->key;
+    if (a->tree != b->tree) return a->tree < b->tree;
+    return a->node < b->node;
+}
+
+static void heap_push(qent_t *h, int64_t *sz, qent_t e) {
+    int64_t i = (*sz)++;
+    h[i] = e;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!qent_less(&h[i], &h[p])) break;
+        qent_t t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+
+static qent_t heap_pop(qent_t *h, int64_t *sz) {
+    qent_t top = h[0];
+    h[0] = h[--(*sz)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, b = i;
+        if (l < *sz && qent_less(&h[l], &h[b])) b = l;
+        if (r < *sz && qent_less(&h[r], &h[b])) b = r;
+        if (b == i) break;
+        qent_t t = h[i]; h[i] = h[b]; h[b] = t;
+        i = b;
+    }
+    return top;
+}
+
+typedef struct {
+    res_t *best;   /* k best so far, sorted by (dist, id) */
+    int32_t nb, k;
+} kbest_t;
+
+static void kbest_insert(kbest_t *H, res_t r) {
+    if (H->nb == H->k && res_cmp(&r, &H->best[H->k - 1]) >= 0) return;
+    int32_t pos = H->nb < H->k ? H->nb++ : H->k - 1;
+    while (pos > 0 && res_cmp(&r, &H->best[pos - 1]) < 0) { H->best[pos] = H->best[pos - 1]; pos--; }
+    H->best[pos] = r;
+}
+
+void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
+                         const float *split_val, const int32_t *perm, int32_t L, int32_t T,
+                         const float *Q, int64_t m, int32_t k, int64_t c, double eps,
+                         int64_t *out_ids, double *out_d, int64_t *ncand, int64_t *nleaves) {
+    int64_t nn = ((int64_t)1 << L) - 1;
+    double budget = (double)c / (1.0 + eps);
+#pragma omp parallel
+    {
+        unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+        int64_t hcap = (int64_t)T * (L + 1) + (int64_t)(budget + T + 1) * (L + 1) + 16;
+        qent_t *heap = (qent_t *)malloc(sizeof(qent_t) * (size_t)hcap);
+        res_t *best = (res_t *)malloc(sizeof(res_t) * (size_t)k);
+        int32_t *touched = NULL;
+        int64_t tcap = 0;
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < m; i++) {
+            const float *q = Q + i * d;
+            int64_t hs = 0, checked = 0, nc = 0, ntouch = 0;
+            kbest_t H = {best, 0, k};
+            /* one descent from node j of tree t to a leaf, pushing the siblings, checking the leaf */
+#define GFO_DESCEND(t_, j_)                                                                        \
+            do {                                                                                   \
+                int64_t j = (j_);                                                                  \
+                const int32_t *sd = split_dim + (int64_t)(t_) * nn;                                \
+                const float *sv = split_val + (int64_t)(t_) * nn;                                  \
+                while (j < nn) {                                                                   \
+                    double dd = (double)q[sd[j]] - (double)sv[j];                                  \
+                    qent_t e;                                                                      \
+                    e.key = fabs(dd);                                                              \
+                    e.tree = (t_);                                                                 \
+                    if (q[sd[j]] < sv[j]) { e.node = 2 * j + 2; j = 2 * j + 1; }                   \
+                    else { e.node = 2 * j + 1; j = 2 * j + 2; }                                    \
+                    heap_push(heap, &hs, e);                                                       \
+                }                                                                                  \
+                int64_t b = j - nn;                                                                \
+                int64_t lo = pos_of(n, L, b), hi = pos_of(n, L, b + 1);                            \
+                for (int64_t p = lo; p < hi; p++) {                                                \
+                    int32_t id = perm[(int64_t)(t_) * n + p];                                      \
+                    if (seen[id]) continue;                                                        \
+                    seen[id] = 1;                                                                  \
+                    if (ntouch == tcap) {                                                          \
+                        tcap = tcap ? 2 * tcap : 4096;                                             \
+                        touched = (int32_t *)realloc(touched, sizeof(int32_t) * (size_t)tcap);     \
+                    }                                                                              \
+                    touched[ntouch++] = id;                                                        \
+                    res_t r = {gfo_dist2(q, X + (int64_t)id * d, d), id};                          \
+                    kbest_insert(&H, r);                                                           \
+                    nc++;                                                                          \
+                }                                                                                  \
+                checked++;                                                                         \
+            } while (0)
+            for (int32_t t = 0; t < T; t++) GFO_DESCEND(t, 0);
+            while (hs > 0 && (double)checked < budget) {
+                if (hs + L + 1 > hcap) break;
+                qent_t e = heap_pop(heap, &hs);
+                GFO_DESCEND(e.tree, e.node);
+            }
+#undef GFO_DESCEND
+            for (int32_t j = 0; j < k; j++) {
+                if (j < H.nb) { out_ids[i * k + j] = H.best[j].id; out_d[i * k + j] = H.best[j].dist; }
+                else { out_ids[i * k + j] = -1; out_d[i * k + j] = INFINITY; }
+            }
+            for (int64_t u = 0; u < ntouch; u++) seen[touched[u]] = 0;
+            if (ncand) ncand[i] = nc;
+            if (nleaves) nleaves[i] = checked;
+        }
+        free(seen);
+        free(heap);
+        free(best);
+        free(touched);
+    }
+}
+
 /* ------------------------------------------------------------------ exact reference */
 
 /*

@@ -56,19 +56,25 @@ def fp8_quantize(X: np.ndarray):
     return scale.astype(np.float32), e4m3_round(Y)
 
 
+def dequantized_rows(X: np.ndarray, rows: np.ndarray, precision: str) -> np.ndarray:
+    """float64 values the screen of `precision` sees for the given rows of X."""
+    Xr = np.ascontiguousarray(X[rows], dtype=np.float32)
+    if precision == "bf16":
+        return bf16_round(Xr).astype(np.float64)
+    if precision == "fp8":
+        scale, codes = fp8_quantize(Xr)
+        return codes * scale.astype(np.float64)[:, None]
+    if precision == "fp32":
+        return Xr.astype(np.float64)
+    raise ValueError(precision)
+
+
 def screened_search(F, X, Q, k, R, precision: str, offs=None, cand=None):
     """Candidates of the forest, screened ranking, shortlist of R, exact rerank, top-k."""
-    X = np.ascontiguousarray(X, dtype=np.float32)
+    X = np.asarray(X)
     Q = np.ascontiguousarray(Q, dtype=np.float32)
     if offs is None:
         offs, cand = oracle.candidates(F, oracle.descend(F, Q))
-    if precision == "bf16":
-        deq = bf16_round(X).astype(np.float64)
-    elif precision == "fp8":
-        scale, codes = fp8_quantize(X)
-        deq = codes * scale.astype(np.float64)[:, None]
-    else:
-        raise ValueError(precision)
     m = Q.shape[0]
     ids = np.full((m, k), -1, dtype=np.int64)
     dd = np.full((m, k), np.inf)
@@ -76,7 +82,7 @@ def screened_search(F, X, Q, k, R, precision: str, offs=None, cand=None):
     for i in range(m):
         c = cand[offs[i]:offs[i + 1]].astype(np.int64)
         q = Q[i].astype(np.float64)
-        sd = ((deq[c] - q) ** 2).sum(axis=1)
+        sd = ((dequantized_rows(X, c, precision) - q) ** 2).sum(axis=1)
         order = np.lexsort((c, sd))[:R]
         sl = c[order]
         shortlist.append((sl, sd[order]))

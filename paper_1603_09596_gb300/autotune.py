@@ -17,7 +17,8 @@ from . import gf
 
 _cache: dict = {}
 
-SHAPES = [(4, 0), (8, 0), (8, 2), (8, 3), (16, 0), (16, 1), (4, 4), (8, 4)]
+# (warps per CTA, CTAs per SM (0 = occupancy), rows in flight per warp (0 = default))
+SHAPES = [(w, c, g) for w in (4, 8) for c in (0, 2, 3) for g in (0, 2, 4)] + [(16, 0, 0), (16, 1, 0)]
 R_CHOICES = [16, 32, 64, 128, 256]
 
 
@@ -41,7 +42,8 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
     key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0])
     if key in _cache:
         res = _cache[key]
-        gf.gf_forest_set_tuning(F, precision, res["warps"], res["ctas_per_sm"], res.get("R", 0))
+        gf.gf_forest_set_tuning(F, precision, res["warps"], res["ctas_per_sm"], res.get("R", 0),
+                                res["rows_in_flight"])
         return res
     res: dict = {"precision": precision}
     R = 0
@@ -59,15 +61,16 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
                 break
         res["R"] = R
     timings = {}
-    for w, c in shapes:
+    for w, c, g in shapes:
         try:
             t = _time(lambda: gf.gf_query(F, Q, k, precision=precision, rerank_R=R, warps_per_cta=w,
-                                          ctas_per_sm=c))
+                                          ctas_per_sm=c, rows_in_flight=g))
         except gf.GFError:
             continue
-        timings[(w, c)] = t
-    (w, c), t = min(timings.items(), key=lambda kv: kv[1])
-    res.update(warps=w, ctas_per_sm=c, ms=t, timings={f"{a}x{b}": v for (a, b), v in timings.items()})
-    gf.gf_forest_set_tuning(F, precision, w, c, R)
+        timings[(w, c, g)] = t
+    (w, c, g), t = min(timings.items(), key=lambda kv: kv[1])
+    res.update(warps=w, ctas_per_sm=c, rows_in_flight=g, ms=t,
+               timings={f"{a}x{b}x{e}": v for (a, b, e), v in timings.items()})
+    gf.gf_forest_set_tuning(F, precision, w, c, R, g)
     _cache[key] = res
     return res

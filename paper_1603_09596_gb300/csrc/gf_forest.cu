@@ -228,13 +228,15 @@ extern "C" int gf_forest_free(gf_forest *F) {
 }
 
 extern "C" int gf_forest_set_tuning(gf_forest *F, int32_t precision, int32_t warps_per_cta,
-                                    int32_t ctas_per_sm, int32_t rerank_R) {
+                                    int32_t ctas_per_sm, int32_t rerank_R, int32_t rows_in_flight) {
     if (!F || precision < 0 || precision > 2) return gf_fail(GF_EINVAL, "bad forest or precision");
-    if (warps_per_cta < 1 || warps_per_cta > 32 || ctas_per_sm < 0 || rerank_R < 0)
+    if (warps_per_cta < 1 || warps_per_cta > 32 || ctas_per_sm < 0 || rerank_R < 0 ||
+        (rows_in_flight != 0 && rows_in_flight != 2 && rows_in_flight != 4))
         return gf_fail(GF_EINVAL, "bad tuning values");
     F->tune_warps[precision] = warps_per_cta;
     F->tune_ctas[precision] = ctas_per_sm;
     if (rerank_R > 0) F->tune_R[precision] = rerank_R;
+    if (rows_in_flight > 0) F->tune_G[precision] = rows_in_flight;
     return GF_OK;
 }
 
@@ -323,6 +325,7 @@ extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_
     x.workspace = o->workspace;
     x.workspace_bytes = o->workspace_bytes;
     x.ncand_out = o->ncand_out;
+    x.rows_in_flight = o->rows_in_flight > 0 ? o->rows_in_flight : F->tune_G[p];
     return gf_launch_query(F, Q, m, k, p, R, warps, cps, (cudaStream_t)o->stream, ids, dists, x);
 }
 

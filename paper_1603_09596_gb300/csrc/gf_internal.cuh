@@ -37,6 +37,7 @@ struct gf_forest {
     int32_t tune_warps[3] = {8, 8, 8};
     int32_t tune_ctas[3] = {0, 0, 0};
     int32_t tune_R[3] = {0, 64, 128};
+    int32_t tune_G[3] = {0, 0, 0};  // rows in flight per warp, 0 = kernel default
     int64_t device_bytes = 0;
 };
 
@@ -98,6 +99,7 @@ struct QueryExtra {
     void *workspace = nullptr;
     int64_t workspace_bytes = 0;
     int32_t *ncand_out = nullptr;
+    int32_t rows_in_flight = 0;
 };
 
 int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,

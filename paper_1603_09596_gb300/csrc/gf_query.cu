@@ -470,30 +470,44 @@ __global__ void k_query_fused(ForestView F, const float *__restrict__ Q, long lo
 
 // ---------------------------------------------------------------- streaming path
 //
-// For candidate sets of any size.  The CTA walks the concatenated leaf ranges of its query in
-// chunks of 32 positions per warp.  A bitmap over the point ids in global memory -- one per CTA,
-// the "seen" array of Sec. 2.3 -- admits every id once (atomicOr test-and-set); admitted rows are
-// scored two at a time per warp and their keys appended to a shared buffer when they beat the
-// running threshold.  When the buffer fills, a radix select keeps the best `keep` keys and raises
-// the threshold.  At the end the kept keys are sorted (and, for a screened precision, rescored in
-// float32) and the bits the query set are cleared again, so the bitmap is all zero between queries.
+// For candidate sets of any size.  The query's leaf positions (the concatenated leaf ranges of the
+// T trees) are processed in phases of LIST positions:
+//   A. every thread takes positions of the phase, reads their ids from the permutations and
+//      test-and-sets them in a bitmap over the point ids -- one per CTA in device memory, the
+//      "seen" array of Sec. 2.3 -- so each id is admitted once per query; admitted ids are packed
+//      into a shared list;
+//   B. the warps score the listed rows, G rows in flight per warp, and append the keys that beat
+//      the running threshold to a shared buffer (no barrier inside the phase);
+//   then, if the buffer holds more than `keep` keys, a radix select keeps the best `keep` and
+//   raises the threshold.  After the last phase the kept keys are sorted (a screened precision
+//   rescores its R best in float32) and the query's bits are cleared, so the bitmap is all zero
+//   between queries.
+
+constexpr int LIST = 2048;  // positions per phase
 
 struct StreamLayout {
-    size_t buf, qs, pref, lofs, lcnt, lpos, hist, wtmp, sh, total;
+    size_t buf, list, qs, pref, lofs, lcnt, lpos, hist, wtmp, sh, total;
 };
 
+// Every region starts on a 16-byte boundary (the query row is read as float4, the keys as u64).
 __host__ __device__ inline StreamLayout stream_layout(int d, int T, int buf_len) {
     StreamLayout L;
     size_t o = 0;
-    L.buf = o;  o += (size_t)buf_len * 8;
-    L.qs = o;   o += (size_t)ldq_of(d) * 4;
-    L.pref = o; o += 16;  // select prefix, threshold
-    L.lofs = o; o += (size_t)T * 4;
-    L.lcnt = o; o += (size_t)T * 4;
-    L.lpos = o; o += (size_t)(T + 1) * 4;
-    L.hist = o; o += 256 * 4;
-    L.wtmp = o; o += 64 * 4;
-    L.sh = o;   o += 8 * 4;
+    auto take = [&o](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    L.buf = take((size_t)buf_len * 8);
+    L.list = take((size_t)LIST * 4);
+    L.qs = take((size_t)ldq_of(d) * 4);
+    L.pref = take(16);  // select prefix, threshold
+    L.lofs = take((size_t)T * 4);
+    L.lcnt = take((size_t)T * 4);
+    L.lpos = take((size_t)(T + 1) * 4);
+    L.hist = take(256 * 4);
+    L.wtmp = take(64 * 4);
+    L.sh = take(8 * 4);
     L.total = o;
     return L;
 }
@@ -507,6 +521,11 @@ __device__ __forceinline__ int tree_of_pos(const int *lpos, int T, int pos) {
         else hi = mid;
     }
     return lo;
+}
+
+__device__ __forceinline__ int id_at(const ForestView &F, const int *lpos, const int *lofs, int pos) {
+    const int t = tree_of_pos(lpos, F.T, pos);
+    return __ldg(F.perm + (size_t)t * F.n + lofs[t] + (pos - lpos[t]));
 }
 
 // In-place stable compaction of buf[0..cnt) to the keys <= kth.
@@ -535,13 +554,90 @@ __device__ void compact_le(unsigned long long *buf, int cnt, unsigned long long 
     }
 }
 
-template <int PREC, int NC, int NCF>
-__global__ void k_query_stream(ForestView F, const float *__restrict__ Q, long long m, int k, int R,
-                               int buf_len, unsigned *bitmaps, int nwords, long long *ids, float *dists,
-                               int *ncand_out) {
+// Squared distances of the query (shared memory) to G rows at once, by the whole warp; every lane
+// returns all G sums.  NC > 0: at most NC 16-byte chunks per lane; NC == 0: any row length.
+template <int PREC, int NC, int G>
+__device__ __forceinline__ void warp_dist_g(const ForestView &F, const float *qs, const int (&ids)[G],
+                                            float (&d)[G]) {
+    constexpr int QF4 = Prec<PREC>::QF4;
+    const int lane = threadIdx.x & 31;
+    const size_t pitch = row_pitch<PREC>(F);
+    const int nch = (int)(pitch >> 4);
+    const unsigned char *base = row_base<PREC>(F);
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+    float4 acc[G];
+    float sc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sc[g] = PREC == P_FP8 ? __ldg(F.scale8 + ids[g]) : 0.f;
+    }
+    constexpr int UB = NC > 0 ? NC : 2;
+    for (int c0 = lane; c0 < nch; c0 += 32 * UB) {
+        uint4 x[G][UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int cc = c0 + 32 * u;
+            if (cc < nch) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) x[g][u] = ld_u4(base + (size_t)ids[g] * pitch + ((size_t)cc << 4));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int cc = c0 + 32 * u;
+            if (cc < nch) {
+                float4 qa[QF4];
+#pragma unroll
+                for (int h = 0; h < QF4; ++h) qa[h] = q4[cc * QF4 + h];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (PREC == P_F32) {
+                        acc4(acc[g], qa[0], *reinterpret_cast<const float4 *>(&x[g][u]));
+                    } else if (PREC == P_BF16) {
+                        acc_bf16(acc[g], qa[0], qa[1], x[g][u]);
+                    } else {
+                        acc_fp8w(acc[g], qa[0], x[g][u].x, sc[g]);
+                        acc_fp8w(acc[g], qa[1], x[g][u].y, sc[g]);
+                        acc_fp8w(acc[g], qa[2], x[g][u].z, sc[g]);
+                        acc_fp8w(acc[g], qa[3], x[g][u].w, sc[g]);
+                    }
+                }
+            }
+        }
+        if (NC > 0) break;  // one pass covers the row
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) d[g] = warp_sum(sum4(acc[g]));
+}
+
+// float32 keys of rows ids[0..C) (all valid), G rows in flight per warp, query in shared memory
+template <int NCF>
+__device__ void rescore_f32(const ForestView &F, const float *qs, const int *ids, int C, unsigned long long *keys) {
+    constexpr int G = (NCF >= 8) ? 2 : 4;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j0 = w * G; j0 < C; j0 += nw * G) {
+        int rid[G];
+        float dd[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) rid[g] = ids[min(j0 + g, C - 1)];
+        warp_dist_g<P_F32, NCF, G>(F, qs, rid, dd);
+        if (lane == 0) {
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (j0 + g < C) keys[j0 + g] = make_key(dd[g], rid[g]);
+        }
+    }
+}
+
+template <int PREC, int NC, int NCF, int G>
+__global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const float *__restrict__ Q, long long m,
+                                                      int k, int R, int buf_len, unsigned *bitmaps, int nwords,
+                                                      long long *ids, float *dists, int *ncand_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const StreamLayout Ly = stream_layout(F.d, F.T, buf_len);
     unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem_raw + Ly.buf);
+    int *list = reinterpret_cast<int *>(smem_raw + Ly.list);
     float *qs = reinterpret_cast<float *>(smem_raw + Ly.qs);
     unsigned long long *pref = reinterpret_cast<unsigned long long *>(smem_raw + Ly.pref);
     unsigned long long *thr = pref + 1;
@@ -550,12 +646,12 @@ __global__ void k_query_stream(ForestView F, const float *__restrict__ Q, long l
     int *lpos = reinterpret_cast<int *>(smem_raw + Ly.lpos);
     unsigned *hist = reinterpret_cast<unsigned *>(smem_raw + Ly.hist);
     int *wtmp = reinterpret_cast<int *>(smem_raw + Ly.wtmp);
-    int *sh = reinterpret_cast<int *>(smem_raw + Ly.sh);  // [0] scratch [1] count [2] total [3] fresh [4] select
-    int *sl = reinterpret_cast<int *>(buf + buf_len / 2);  // shortlist ids (upper half of buf)
+    // sh: [0] compaction scratch [1] buffer count [2] positions [3] admitted ids [4] select [5] list count
+    int *sh = reinterpret_cast<int *>(smem_raw + Ly.sh);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int keep = PREC == P_F32 ? k : R;
-    const int limit = buf_len - 32 * nw;
     unsigned *bm = bitmaps + (size_t)blockIdx.x * nwords;
+    const unsigned lt = (1u << lane) - 1u;
 
     for (long long qi = blockIdx.x; qi < m; qi += gridDim.x) {
         load_query(Q + qi * F.d, F.d, qs);
@@ -577,50 +673,56 @@ __global__ void k_query_stream(ForestView F, const float *__restrict__ Q, long l
         }
         __syncthreads();
         const int tot = sh[2];
-        float4 qr[(NC > 0 ? NC : 1) * Prec<PREC>::QF4];
-        load_qreg<PREC, NC>(F, qs, qr);
-        const int nchunk = (tot + 31) >> 5;
-        for (int c0 = 0; c0 < nchunk; c0 += nw) {
-            const int c = c0 + w;
-            if (c < nchunk) {
-                const int pos = (c << 5) + lane;
-                int id = -1;
-                if (pos < tot) {
-                    const int t = tree_of_pos(lpos, F.T, pos);
-                    id = __ldg(F.perm + (size_t)t * F.n + lofs[t] + (pos - lpos[t]));
+        for (int p0 = 0; p0 < tot; p0 += LIST) {
+            // ---- A: admit the phase's ids through the bitmap, pack them into the list
+            if (threadIdx.x == 0) sh[5] = 0;
+            __syncthreads();
+            const int pend = min(LIST, tot - p0);
+            for (int b0 = 0; b0 < pend; b0 += 4 * blockDim.x) {
+                int id[4];
+                unsigned old[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int off = b0 + u * blockDim.x + threadIdx.x;
+                    id[u] = off < pend ? id_at(F, lpos, lofs, p0 + off) : -1;
                 }
-                bool fresh = false;
-                if (id >= 0) {
-                    const unsigned bit = 1u << (id & 31);
-                    fresh = !(atomicOr(bm + (id >> 5), bit) & bit);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    old[u] = id[u] >= 0 ? atomicOr(bm + (id[u] >> 5), 1u << (id[u] & 31)) : ~0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool fresh = id[u] >= 0 && !(old[u] & (1u << (id[u] & 31)));
+                    const unsigned bl = __ballot_sync(FULL, fresh);
+                    int base = 0;
+                    if (lane == 0 && bl) base = atomicAdd(&sh[5], __popc(bl));
+                    base = __shfl_sync(FULL, base, 0);
+                    if (fresh) list[base + __popc(bl & lt)] = id[u];
                 }
-                unsigned mask = __ballot_sync(FULL, fresh);
-                if (lane == 0 && mask) atomicAdd(&sh[3], __popc(mask));
-                while (mask) {
-                    const int b0 = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const bool two = mask != 0;
-                    const int b1 = two ? __ffs(mask) - 1 : b0;
-                    if (two) mask &= mask - 1;
-                    const int i0 = __shfl_sync(FULL, id, b0);
-                    const int i1 = __shfl_sync(FULL, id, b1);
-                    float d0, d1;
-                    warp_dist2<PREC, NC>(F, qr, qs, i0, i1, d0, d1);
-                    if (lane == 0) {
-                        const unsigned long long th = *reinterpret_cast<volatile unsigned long long *>(thr);
-                        const unsigned long long k0 = make_key(d0, i0);
-                        if (k0 < th) buf[atomicAdd(&sh[1], 1)] = k0;
-                        if (two) {
-                            const unsigned long long k1 = make_key(d1, i1);
-                            if (k1 < th) buf[atomicAdd(&sh[1], 1)] = k1;
-                        }
+            }
+            __syncthreads();
+            const int nl = sh[5];
+            // ---- B: score the admitted rows, G per warp at a time
+            for (int j0 = w * G; j0 < nl; j0 += nw * G) {
+                int rid[G];
+                float dd[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) rid[g] = list[min(j0 + g, nl - 1)];
+                warp_dist_g<PREC, NC, G>(F, qs, rid, dd);
+                if (lane == 0) {
+                    const unsigned long long th = *reinterpret_cast<volatile unsigned long long *>(thr);
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        if (j0 + g >= nl) break;
+                        const unsigned long long key = make_key(dd[g], rid[g]);
+                        if (key < th) buf[atomicAdd(&sh[1], 1)] = key;
                     }
                 }
             }
             __syncthreads();
             const int cnt_now = sh[1];
-            __syncthreads();  // every thread has read the count before any appends again
-            if (cnt_now > limit) {
+            if (threadIdx.x == 0) sh[3] += nl;
+            __syncthreads();  // every thread has read the count before it changes
+            if (cnt_now > keep) {
                 const unsigned long long kth = gfdev::block_select(buf, cnt_now, keep - 1, hist, pref, &sh[4]);
                 compact_le(buf, cnt_now, kth, wtmp, &sh[0]);
                 if (threadIdx.x == 0) {
@@ -630,26 +732,16 @@ __global__ void k_query_stream(ForestView F, const float *__restrict__ Q, long l
                 __syncthreads();
             }
         }
-        __syncthreads();
-        int cnt = sh[1];
-        __syncthreads();
-        if (cnt > keep) {
-            const unsigned long long kth = gfdev::block_select(buf, cnt, keep - 1, hist, pref, &sh[4]);
-            compact_le(buf, cnt, kth, wtmp, &sh[0]);
-            cnt = keep;
-        }
+        const int cnt = min(sh[1], keep);
         sort_keys(buf, cnt);
         if (PREC != P_F32) {
-            for (int j = threadIdx.x; j < cnt; j += blockDim.x) sl[j] = (int)(unsigned)(buf[j] & 0xffffffffu);
+            for (int j = threadIdx.x; j < cnt; j += blockDim.x) list[j] = (int)(unsigned)(buf[j] & 0xffffffffu);
             __syncthreads();
-            score_rows<P_F32, NCF>(F, qs, sl, cnt, buf);
+            rescore_f32<NCF>(F, qs, list, cnt, buf);
             sort_keys(buf, cnt);
         }
         write_topk(buf, cnt, k, ids + qi * k, dists + qi * k);
-        for (int pos = threadIdx.x; pos < tot; pos += blockDim.x) {
-            const int t = tree_of_pos(lpos, F.T, pos);
-            bm[__ldg(F.perm + (size_t)t * F.n + lofs[t] + (pos - lpos[t])) >> 5] = 0u;
-        }
+        for (int pos = threadIdx.x; pos < tot; pos += blockDim.x) bm[id_at(F, lpos, lofs, pos) >> 5] = 0u;
         if (threadIdx.x == 0 && ncand_out) ncand_out[qi] = sh[3];
         __syncthreads();
     }
@@ -711,22 +803,25 @@ int launch_fused(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32
     return GF_OK;
 }
 
-int stream_buf_len(int keep, int warps) {
-    int kp = 1;
-    while (kp < keep) kp <<= 1;
-    return next_pow2(std::max(2048, 2 * (kp + 32 * warps)));
-}
+// buffer: the kept keys plus one phase of appends
+int stream_buf_len(int keep) { return keep + LIST; }
 
-template <int PREC, int NC, int NCF>
-int launch_stream(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
-                  int ctas_per_sm, cudaStream_t st, int64_t *ids, float *dists, const QueryExtra &x,
-                  long long *grid_only = nullptr) {
+// default rows in flight per warp: four when a lane holds at most two 16-byte chunks of a row,
+// else two (more would spill registers)
+int default_rows_in_flight(int nc) { return (nc == 0 || nc >= 4) ? 2 : 4; }
+
+template <int PREC, int NC, int NCF, int G>
+int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
+                    int ctas_per_sm, cudaStream_t st, int64_t *ids, float *dists, const QueryExtra &x,
+                    long long *grid_only) {
     const int keep = PREC == P_F32 ? k : R;
-    const int buf_len = stream_buf_len(keep, warps);
+    if (keep > LIST) return gf_fail(GF_EUNSUPPORTED, "k or R = %d above %d", keep, LIST);
+    const int buf_len = stream_buf_len(keep);
     const size_t smem = stream_layout(F->d, F->T, buf_len).total;
     int r = check_smem(F, smem);
     if (r) return r;
-    auto kern = k_query_stream<PREC, NC, NCF>;
+    if (warps > 8) return gf_fail(GF_EINVAL, "warps_per_cta=%d above 8 for the streaming kernel", warps);
+    auto kern = k_query_stream<PREC, NC, NCF, G>;
     if ((r = prep_kernel(kern, smem))) return r;
     const int threads = warps * 32;
     cudaFuncAttributes fa;
@@ -768,6 +863,16 @@ int launch_stream(const gf_forest *F, const float *Q, int64_t m, int32_t k, int3
     if (own) cudaFreeAsync(bitmaps, st);
     if (e != cudaSuccess) return gf_cuda_fail(e, "k_query_stream launch");
     return GF_OK;
+}
+
+template <int PREC, int NC, int NCF>
+int launch_stream(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
+                  int ctas_per_sm, cudaStream_t st, int64_t *ids, float *dists, const QueryExtra &x,
+                  long long *grid_only = nullptr) {
+    const int g = x.rows_in_flight > 0 ? x.rows_in_flight : default_rows_in_flight(NC);
+    if (g == 2) return launch_stream_g<PREC, NC, NCF, 2>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x, grid_only);
+    if (g == 4) return launch_stream_g<PREC, NC, NCF, 4>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x, grid_only);
+    return gf_fail(GF_EINVAL, "rows_in_flight=%d (2 or 4)", g);
 }
 
 template <int PREC>

@@ -37,7 +37,7 @@ GF_ALGO_AUTO, GF_ALGO_SORT, GF_ALGO_STREAM = 0, 1, 2
 class QueryOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rerank_R", C.c_int32), ("warps_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("stream", C.c_void_p), ("algo", C.c_int32),
-                ("reserved", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64),
+                ("rows_in_flight", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64),
                 ("ncand_out", C.c_void_p)]
 
 
@@ -80,7 +80,7 @@ def lib() -> C.CDLL:
             "gf_forest_export": ([P, P, P, P], i32),
             "gf_forest_get_info": ([P, P], i32),
             "gf_forest_add_screen": ([P, i32, P], i32),
-            "gf_forest_set_tuning": ([P, i32, i32, i32, i32], i32),
+            "gf_forest_set_tuning": ([P, i32, i32, i32, i32, i32], i32),
             "gf_forest_free": ([P], i32),
             "gf_query": ([P, P, i64, i32, P, P], i32),
             "gf_query_ex": ([P, P, i64, i32, P, P, P], i32),
@@ -206,12 +206,15 @@ def gf_forest_add_screen(F: Forest, precision: int, stream=None) -> None:
 
 
 def gf_forest_set_tuning(F: Forest, precision: int, warps_per_cta: int, ctas_per_sm: int,
-                         rerank_R: int) -> None:
-    _check(lib().gf_forest_set_tuning(F.handle, precision, warps_per_cta, ctas_per_sm, rerank_R))
+                         rerank_R: int, rows_in_flight: int = 0) -> None:
+    _check(lib().gf_forest_set_tuning(F.handle, precision, warps_per_cta, ctas_per_sm, rerank_R,
+                                      rows_in_flight))
 
 
-def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out):
-    o = QueryOpts(precision, rerank_R, warps_per_cta, ctas_per_sm, _stream(stream), algo, 0, None, 0, None)
+def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
+          rows_in_flight=0):
+    o = QueryOpts(precision, rerank_R, warps_per_cta, ctas_per_sm, _stream(stream), algo, rows_in_flight,
+                  None, 0, None)
     if workspace is not None:
         o.workspace = _dptr(workspace, workspace.dtype, "workspace")
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -223,7 +226,7 @@ def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspa
 def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, rerank_R: int = 0,
              warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None, algo: int = GF_ALGO_AUTO,
              workspace: torch.Tensor | None = None, ncand_out: torch.Tensor | None = None,
-             out: tuple[torch.Tensor, torch.Tensor] | None = None):
+             rows_in_flight: int = 0, out: tuple[torch.Tensor, torch.Tensor] | None = None):
     """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k])."""
     m = Q.shape[0]
     if out is None:
@@ -231,7 +234,8 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
         dists = torch.empty((m, k), dtype=torch.float32, device=Q.device)
     else:
         ids, dists = out
-    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out)
+    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
+              rows_in_flight)
     _check(lib().gf_query_ex(F.handle, _dptr(Q, torch.float32, "Q"), m, k, C.byref(o),
                              _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists")))
     return ids, dists
@@ -306,7 +310,7 @@ class Server:
     def submit(self, forest: int, q, k: int) -> int:
         import numpy as np
         q = np.ascontiguousarray(q, dtype=np.float32)
-        if q.shape != (self.dims[forest],):
+        if 0 <= forest < len(self.dims) and q.shape != (self.dims[forest],):
             raise ValueError("query has the wrong length")
         t = C.c_uint64()
         _check(lib().gf_server_submit(self.handle, forest, q.ctypes.data, k, C.byref(t)))

@@ -226,16 +226,9 @@ def test_screened_distances_elementwise(gf, prec, name):
     nc = np.diff(offs).astype(np.int32)
     dist = gf.gf_score_screened(G, torch.from_numpy(Q).cuda(), torch.from_numpy(cand).cuda(),
                                 torch.from_numpy(nc).cuda(), gf.PRECISIONS[prec]).cpu().numpy()
-    if prec == "fp32":
-        deq = X.astype(np.float64)
-    elif prec == "bf16":
-        deq = screen.bf16_round(X).astype(np.float64)
-    else:
-        sc, codes = screen.fp8_quantize(X)
-        deq = codes * sc.astype(np.float64)[:, None]
     for i in range(m):
         c = cand[i, :nc[i]]
-        ref = ((deq[c] - Q[i].astype(np.float64)) ** 2).sum(axis=1)
+        ref = ((screen.dequantized_rows(X, c, prec) - Q[i].astype(np.float64)) ** 2).sum(axis=1)
         np.testing.assert_allclose(dist[i, :nc[i]], ref, rtol=RTOL, atol=RTOL * ref.max())
 
 
@@ -266,8 +259,9 @@ def test_stream_equals_sort_kernel(gf, prec, name):
         gf.gf_forest_add_screen(G, p)
     Qg = torch.from_numpy(Q).cuda()
     a = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_SORT)
-    b = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_STREAM)
-    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    for g in (2, 4):
+        b = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_STREAM, rows_in_flight=g)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
 def test_stream_caller_workspace_is_left_zero(gf):

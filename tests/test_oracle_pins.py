@@ -286,3 +286,46 @@ def test_recall_metrics():
     wrong = ei.copy()
     wrong[:, 0] = ei[:, 2]
     assert oracle.recall_at_1(wrong, ed, X, Q) < 1.0
+
+
+# ------------------------------------------------------------------ Alg. 2 priority search
+
+def test_priority_search_hand_order(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "hand_2d.json")))
+    X = np.array(g["X"], dtype=np.float32)
+    F = oracle.build_forest(X, 1, 2, t=1, shuffle=0, seed=0)
+    q = np.array([g["priority_query"]], dtype=np.float32)
+    for c, e in g["priority_expect"].items():
+        ids, d, nc, nl = oracle.search_priority(F, X, q, 1, int(c))
+        assert (nl[0], nc[0], ids[0, 0]) == (e["leaves"], e["cand"], e["id"])
+
+
+def test_priority_search_with_c_equal_T_is_one_leaf_per_tree():
+    X, Q = synth.mixture(3000, 24, 40, "B", seed=21)
+    F = oracle.build_forest(X, 6, 30, seed=2)
+    ids, d, nc = oracle.search(F, X, Q, 5, return_ncand=True)
+    pi, pd, pnc, pnl = oracle.search_priority(F, X, Q, 5, F.T)
+    assert np.array_equal(pi, ids) and np.array_equal(pd, d) and np.array_equal(pnc, nc)
+    assert np.all(pnl == F.T)
+
+
+def test_priority_search_all_leaves_is_exact():
+    X, Q = synth.mixture(600, 12, 30, "A", seed=22)
+    F = oracle.build_forest(X, 2, 20, seed=1)
+    ids, d, nc, nl = oracle.search_priority(F, X, Q, 4, F.T << F.L)
+    ei, ed = oracle.bruteforce(X, Q, 4)
+    assert np.array_equal(ids, ei) and np.all(nc == 600)
+
+
+def test_priority_search_budget_and_monotonicity():
+    X, Q = synth.mixture(4000, 32, 50, "B", seed=23)
+    F = oracle.build_forest(X, 4, 25, seed=3)
+    prev = np.full(Q.shape[0], np.inf)
+    for c in (4, 8, 16, 40, 100):
+        ids, d, nc, nl = oracle.search_priority(F, X, Q, 1, c)
+        assert np.all(nl == c)
+        assert np.all(d[:, 0] <= prev)
+        prev = d[:, 0]
+    # c / (1 + eps) leaves: eps = 1 halves the budget (Sec. 2.3)
+    _, _, _, nl = oracle.search_priority(F, X, Q, 1, 40, eps=1.0)
+    assert np.all(nl == 20)
