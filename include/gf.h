@@ -190,6 +190,31 @@ int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_t k, const 
  * of ceil(n / 32) words per CTA of the launch).  o may be NULL for the defaults. */
 int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_query_opts *o, int64_t *bytes);
 
+/* ---------------------------------------------------------------- query without allocation
+ * gf_query_noalloc -- the query of gf_query_ex with GF_ALGO_STREAM, for callers that may not
+ * allocate device memory while they run queries (a framework whose caching allocator must own
+ * every device byte, a latency-critical loop that must stay out of the driver's allocator, a host
+ * that fixes its memory at start-up).  The paper has no counterpart: its search is a single-threaded
+ * CPU routine with no device memory at all.
+ *
+ * The kernel's scratch (one seen-bitmap of ceil(n / 32) 32-bit words per CTA) comes from a static
+ * device array of GF_NOALLOC_SCRATCH_BYTES that is part of the library image: every GPU that loads
+ * the library holds it until the process exits.  The queries run in consecutive launches of at
+ * most GF_NOALLOC_SCRATCH_BYTES / (4 * ceil(n / 32)) rows each, so a forest of more than
+ * 8 * GF_NOALLOC_SCRATCH_BYTES points (536,870,912) is rejected with GF_EINVAL.  Arguments,
+ * outputs and errors are those of gf_query_ex; precision and rerank_R as in gf_query_opts.
+ *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture on the device.
+ *  - The array is shared by every call in the process and keeps what the last call left in it;
+ *    each call clears the part it uses before its kernels run.  Calls whose work overlaps on the GPU
+ *    (on different streams, or from several threads) race on the array and give wrong answers:
+ *    order them on one stream or synchronize between them.
+ */
+#define GF_NOALLOC_SCRATCH_BYTES (64ll << 20)
+
+int gf_query_noalloc(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,
+                     int32_t rerank_R, void *stream, int64_t *ids, float *dists);
+
 /* ---------------------------------------------------------------- the path in stages
  * The same computation as gf_query, one step per call, with the intermediate results in caller
  * buffers (used to check every step on its own).  All asynchronous on `stream`.
