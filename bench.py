@@ -101,6 +101,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate(ms_local: float, m_local: int, world: int, device=None):
+    """Whole-job throughput over N replicas: every rank answered m_local queries; the job's time is
+    the slowest rank's (max over ranks).  Returns (queries/s, max ms)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * m_local / (ms / 1e3), ms
+
+
 def exact_nn(torch, Xg, Qs, k):
     """Exact k-NN of the sample Qs (evaluation only): float32 GEMM shortlist, float64 recheck."""
     xn = (Xg * Xg).sum(1)
@@ -126,6 +139,63 @@ def recall(torch, Xg, Qs, ids, exact_i, exact_d):
     k = exact_i.shape[1]
     hits = (ids[:, :, None] == exact_i[:, None, :]).any(-1).double().sum(1) / k
     return r1, float(hits.mean())
+
+
+def time_batch(gf, F, Qg, k, prec, steps, warmup, dev, world=1, local=0, no_graph=False):
+    """Time `steps` launches of the batch Qg; the launch is captured once in a CUDA graph (with a
+    caller workspace, so nothing allocates inside the capture) and replayed per step."""
+    import torch
+    m = Qg.shape[0]
+    ids = torch.empty((m, k), dtype=torch.int64, device=dev)
+    dd = torch.empty((m, k), dtype=torch.float32, device=dev)
+    ws = torch.zeros(gf.gf_query_workspace_size(F, m, precision=prec) // 4 + 1, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+
+    def launch():
+        gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd), workspace=ws, stream=s)
+
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            launch()
+    torch.cuda.synchronize()
+    graph = None
+    if not no_graph:
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                launch()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(s):
+                graph.replay()
+            torch.cuda.synchronize()
+        except Exception as e:  # capture not possible here: time direct launches
+            print(f"cuda graph capture failed, timing direct launches: {e}", file=sys.stderr)
+            graph = None
+            torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with Clocks(local) as ck:
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for a, b in evs:
+                a.record(s)
+                graph.replay() if graph is not None else launch()
+                b.record(s)
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return ids, dd, ms, dict(ck.summary(), launch="cuda_graph" if graph is not None else "direct")
+
+
+def query_bytes(gf, F, prec, C, R, d, k):
+    """Algorithmic bytes of one query: candidate rows in the scored precision, the float32 rerank
+    rows, the query, the leaf ids read from the permutations and the results."""
+    inf = F.info
+    positions = inf.T * (inf.n / (1 << inf.L))
+    b = {gf.GF_FP32: 4, gf.GF_BF16_RERANK: 2, gf.GF_FP8_RERANK: 1}[prec]
+    rows = C * (d * b + (4 if prec == gf.GF_FP8_RERANK else 0))
+    rerank = R * d * 4 if prec != gf.GF_FP32 else 0
+    return rows + rerank + d * 4 + positions * 4 + 12 * k
 
 
 def ours(args):
@@ -156,54 +226,10 @@ def ours(args):
     ei, ed = exact_nn(torch, Xg, Qg[:S], k)
 
     def time_query(F, prec, steps, warmup):
-        """Time `steps` launches of the batch; the launch is captured once in a CUDA graph (with a
-        caller workspace, so nothing allocates inside the capture) and replayed per step."""
-        ids = torch.empty((m, k), dtype=torch.int64, device=dev)
-        dd = torch.empty((m, k), dtype=torch.float32, device=dev)
-        ws = torch.zeros(gf.gf_query_workspace_size(F, m, precision=prec) // 4 + 1, dtype=torch.int32, device=dev)
-        s = torch.cuda.Stream(device=dev)
-
-        def launch():
-            gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd), workspace=ws, stream=s)
-
-        with torch.cuda.stream(s):
-            for _ in range(warmup):
-                launch()
-        torch.cuda.synchronize()
-        graph = None
-        if not args.no_graph:
-            try:
-                graph = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(graph, stream=s):
-                    launch()
-                torch.cuda.synchronize()
-                with torch.cuda.stream(s):
-                    graph.replay()
-                torch.cuda.synchronize()
-            except Exception as e:  # capture not possible here: time direct launches
-                print(f"cuda graph capture failed, timing direct launches: {e}", file=sys.stderr)
-                graph = None
-                torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        with Clocks(local) as ck:
-            torch.cuda.synchronize()
-            with torch.cuda.stream(s):
-                for a, b in evs:
-                    a.record(s)
-                    graph.replay() if graph is not None else launch()
-                    b.record(s)
-            torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        return ids, dd, ms, dict(ck.summary(), launch="cuda_graph" if graph is not None else "direct")
+        return time_batch(gf, F, Qg, k, prec, steps, warmup, dev, world, local, args.no_graph)
 
     def bytes_per_query(F, prec, C, R):
-        inf = F.info
-        positions = inf.T * (n / (1 << inf.L))       # leaf ids read from the permutations
-        rows = C * d * (2 if prec == gf.GF_BF16_RERANK else 4)
-        rerank = R * d * 4 if prec != gf.GF_FP32 else 0
-        return rows + rerank + d * 4 + positions * 4 + 12 * k
+        return query_bytes(gf, F, prec, C, R, d, k)
 
     def run_forest(T, p, tune_sample):
         torch.cuda.synchronize()
@@ -238,12 +264,7 @@ def ours(args):
     else:
         spec = None
     best = head["bf16"]
-    mean_ms = best["ms_per_step"]
-    if world > 1:
-        t = torch.tensor([mean_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        mean_ms = float(t.item())
-    value = world * m / (mean_ms / 1e3)
+    value, mean_ms = aggregate(best["ms_per_step"], m, world, device=dev)
     achieved = best["bytes_per_query"] * m / (mean_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "traffic": None,
@@ -282,15 +303,15 @@ def ours(args):
     # the measured batch throughput, continuous batching (up to 1024 per batch, 4 slots)
     lat = None
     if not args.no_serve:
-        S = gf.Server([Fh], max_batch=1024, slots=4, hbm_budget_bytes=8 << 30, k_max=k,
-                      precision=gf.GF_BF16_RERANK, rerank_R=best["R"])
+        srv = gf.Server([Fh], max_batch=1024, slots=4, hbm_budget_bytes=8 << 30, k_max=k,
+                        precision=gf.GF_BF16_RERANK, rerank_R=best["R"])
         rate = 0.5 * value / world
-        S.run_poisson([Q[:4096]], rate_qps=min(rate, 5000), duration_s=0.3, k=k, seed=3)
-        st = S.run_poisson([Q], rate_qps=rate, duration_s=args.serve_seconds, k=k, seed=4)
+        srv.run_poisson([Q[:4096]], rate_qps=min(rate, 5000), duration_s=0.3, k=k, seed=3)
+        st = srv.run_poisson([Q], rate_qps=rate, duration_s=args.serve_seconds, k=k, seed=4)
         lat = {"offered_qps": round(rate, 1), "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
                "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 1),
                "completed": st["completed"]}
-        S.close()
+        srv.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -365,6 +386,46 @@ def profile(args):
     print(json.dumps({"profile": True, "n": args.n, "d": args.d, "m": args.m, "T": args.T,
                       "leaf_size": args.leaf_size, "precision": args.precision,
                       "ms_per_launch": a.elapsed_time(b) / args.steps}))
+
+
+def highd(args):
+    """The d = 10^4 workload: float32 vs bf16 vs FP8-E4M3 screening (+ float32 rerank)."""
+    import torch
+    import paper_1603_09596_gb300 as gf
+    from paper_1603_09596_gb300 import autotune
+    import synth
+    n, d, m, T, p, k = 200_000, 10_000, 2_000, 24, 32, 10
+    X, Q = synth.mixture(n, d, m, "C", seed=0, qseed=1)
+    dev = torch.device("cuda", 0)
+    Xg, Qg = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    del X
+    S = min(m, args.recall_sample)
+    ei, ed = exact_nn(torch, Xg, Qg[:S], k)
+    tb = time.time()
+    F = gf.gf_build(Xg, T, p, seed=0)
+    torch.cuda.synchronize()
+    build_s = time.time() - tb
+    gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
+    gf.gf_forest_add_screen(F, gf.GF_FP8_RERANK)
+    nc = torch.empty((m,), dtype=torch.int32, device=dev)
+    gf.gf_query(F, Qg, k, algo=gf.GF_ALGO_STREAM, ncand_out=nc)
+    C = float(nc.double().mean())
+    hbm_peak, _ = peaks()
+    out = {}
+    for name in ("fp32", "bf16", "fp8"):
+        prec = gf.PRECISIONS[name]
+        tr = autotune.tune(F, Qg[:min(m, 1000)], k, prec)
+        ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, no_graph=args.no_graph)
+        r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
+        mean_ms = statistics.mean(ms)
+        bpq = query_bytes(gf, F, prec, C, tr.get("R", 0), d, k)
+        out[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4),
+                     "recall_at_1": r1, "recall_at_10": rk, "R": tr.get("R", 0),
+                     "achieved_gbs": round(bpq * m / (mean_ms / 1e3) / 1e9, 1),
+                     "frac_of_hbm": round(bpq * m / (mean_ms / 1e3) / 1e9 / hbm_peak, 4), "clocks": ck}
+    print(json.dumps({"metric": "queries/s at 2e5 x 1e4, k=10: fp8 / bf16 screen + fp32 rerank vs fp32",
+                      "unit": "queries/s", "n": n, "d": d, "m": m, "T": T, "leaf_size": p,
+                      "cand_per_query": round(C, 1), "build_s": round(build_s, 2), "results": out}))
 
 
 SERVE_FORESTS = [  # (n, d, T, leaf_size): six resident forests of uneven size
@@ -470,6 +531,7 @@ def main():
     ap.add_argument("--profile-rows", type=int, default=0)
     ap.add_argument("--profile-ctas", type=int, default=0)
     ap.add_argument("--serve", action="store_true", help="serving workload (six forests, Poisson load)")
+    ap.add_argument("--highd", action="store_true", help="d = 10^4 workload: fp8 / bf16 / fp32")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB for batch slots")
@@ -478,6 +540,8 @@ def main():
         profile(args)
     elif args.serve:
         serve(args)
+    elif args.highd:
+        highd(args)
     elif args.impl == "reference":
         reference(args)
     else:

@@ -68,6 +68,13 @@ typedef struct gf_rand_params {
 #define GF_ALGO_STREAM 2 /* candidates de-duplicated through a per-CTA bitmap over the point ids
                             in device memory ("seen" array, Sec. 2.3); any candidate count */
 
+/* Order in which the streaming kernel's CTAs take the queries of a batch.  Results do not depend
+ * on it; throughput does: queries that reach the same leaf of tree 0 share most candidates, and
+ * CTAs working on them at the same time find the shared rows in L2. */
+#define GF_ORDER_AUTO 0      /* LOCALITY when the batch has more queries than the launch has CTAs */
+#define GF_ORDER_GIVEN 1     /* as given */
+#define GF_ORDER_LOCALITY 2  /* sorted by the leaf of tree 0 (chunks of 16,384 queries) */
+
 typedef struct gf_query_opts {
     int32_t precision;       /* GF_FP32, GF_BF16_RERANK or GF_FP8_RERANK */
     int32_t rerank_R;        /* shortlist length for the screened precisions; 0 = forest default */
@@ -83,6 +90,8 @@ typedef struct gf_query_opts {
     int64_t workspace_bytes; /* size of `workspace` */
     int32_t *ncand_out;      /* STREAM only, optional: device [m] int32, number of distinct
                                 candidates of each query */
+    int32_t order;           /* STREAM only, GF_ORDER_*: the order in which CTAs take queries */
+    int32_t reserved;
 } gf_query_opts;
 
 typedef struct gf_forest gf_forest; /* opaque; owned by the library */
@@ -186,8 +195,9 @@ int gf_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int64_t *
 int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_t k, const gf_query_opts *o,
                 int64_t *ids, float *dists);
 
-/* Bytes of device scratch a GF_ALGO_STREAM query of m rows needs with these options (one bitmap
- * of ceil(n / 32) words per CTA of the launch).  o may be NULL for the defaults. */
+/* Bytes of device scratch a GF_ALGO_STREAM query of m rows needs with these options: one bitmap of
+ * ceil(n / 32) words per CTA of the launch, plus 12 bytes per query when the batch is reordered
+ * (GF_ORDER_*).  An upper bound for every k.  o may be NULL for the defaults. */
 int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_query_opts *o, int64_t *bytes);
 
 /* ---------------------------------------------------------------- query without allocation

@@ -8,9 +8,9 @@
 // because the sequences start as 0..n-1).
 //
 // Per node:
-//   1. per-dimension variance of the node's points, accumulated in float64 as sums of
-//      (x - K) and (x - K)^2 with K the node's first point (no cancellation), then
-//      var = (S2 - S1^2 / c) / (c - 1);
+//   1. per-dimension variance of the node's points from the sums of (x - K) and (x - K)^2 with K
+//      the node's first point (no cancellation), accumulated as compensated float32 pairs and
+//      combined in float64, then var = (S2 - S1^2 / c) / (c - 1);
 //   2. the t dimensions of largest variance, ranked by (variance desc, index asc), and the split
 //      dimension s = D[u mod t] with u the node's SplitMix64 draw;
 //   3. the split: points ordered by the unique 64-bit key (order-preserving bits of x_s, rk_t(id))
@@ -111,18 +111,54 @@ __device__ __forceinline__ NodeGeo geo(const BuildParams &P, int l, long long se
 
 // ---------------------------------------------------------------- variance
 
-// Shifted sums over rows[0..cnt) for the dims dbase + tid + NT*u, u < DPT.
+// Error-free transformations on float32 (Knuth's TwoSum; Dekker's product with an FMA): the
+// result pair (s, e) satisfies s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated sum hi + lo of float32 terms: hi is the running float32 sum, lo collects every
+// rounding error of hi exactly (plus its own, second-order, rounding).
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add(FF &a, float x, float xlo) {
+    float s, e;
+    two_sum(a.hi, x, s, e);
+    a.hi = s;
+    a.lo += e + xlo;
+}
+
+// Shifted sums over rows[0..cnt) for the dims dbase + tid + NT*u, u < DPT: S1 = sum (x - K),
+// S2 = sum (x - K)^2 with K the node's first point.  Each difference is split exactly into
+// float32 hi + lo, its square into a float32 product plus its exact FMA error (the lo^2 term is
+// below 2^-48 relative and dropped), and both sums are compensated, so the relative error is of
+// order cnt * 2^-48 -- float64 accuracy at float32 instruction rates (GB300's float64 rate is a
+// small fraction of its float32 rate).
 __device__ __forceinline__ void var_accum(const BuildParams &P, const int *__restrict__ rows, long long cnt,
                                           int krow, int dbase, double S1[DPT], double S2[DPT]) {
     float K[DPT];
     int dim[DPT];
+    FF s1[DPT], s2[DPT];
 #pragma unroll
     for (int u = 0; u < DPT; ++u) {
         dim[u] = dbase + threadIdx.x + NT * u;
         K[u] = dim[u] < P.d ? __ldg(P.x + (size_t)krow * P.ldx + dim[u]) : 0.f;
-        S1[u] = 0.0;
-        S2[u] = 0.0;
+        s1[u] = FF{0.f, 0.f};
+        s2[u] = FF{0.f, 0.f};
     }
+    auto add = [&](int u, float x) {
+        float dh, dl;
+        two_sum(x, -K[u], dh, dl);          // x - K = dh + dl exactly
+        const float p = dh * dh;
+        float pe = fmaf(dh, dh, -p);         // dh^2 = p + pe exactly
+        pe = fmaf(2.f * dh, dl, pe);         // + 2 dh dl
+        ff_add(s1[u], dh, dl);
+        ff_add(s2[u], p, pe);
+    };
     long long r = 0;
     for (; r + 4 <= cnt; r += 4) {
         float v[4][DPT];
@@ -135,20 +171,17 @@ __device__ __forceinline__ void var_accum(const BuildParams &P, const int *__res
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int u = 0; u < DPT; ++u) {
-                const double e = (double)v[q][u] - (double)K[u];
-                S1[u] += e;
-                S2[u] = fma(e, e, S2[u]);
-            }
+            for (int u = 0; u < DPT; ++u) add(u, v[q][u]);
     }
     for (; r < cnt; ++r) {
         const float *row = P.x + (size_t)__ldg(rows + r) * P.ldx;
 #pragma unroll
-        for (int u = 0; u < DPT; ++u) {
-            const double e = (double)(dim[u] < P.d ? __ldg(row + dim[u]) : 0.f) - (double)K[u];
-            S1[u] += e;
-            S2[u] = fma(e, e, S2[u]);
-        }
+        for (int u = 0; u < DPT; ++u) add(u, dim[u] < P.d ? __ldg(row + dim[u]) : 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < DPT; ++u) {
+        S1[u] = (double)s1[u].hi + (double)s1[u].lo;
+        S2[u] = (double)s2[u].hi + (double)s2[u].lo;
     }
 }
 

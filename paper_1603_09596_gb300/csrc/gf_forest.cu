@@ -2,6 +2,7 @@
 // points of the C ABI.
 #include "gf_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -326,6 +327,8 @@ extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_
     x.workspace_bytes = o->workspace_bytes;
     x.ncand_out = o->ncand_out;
     x.rows_in_flight = o->rows_in_flight > 0 ? o->rows_in_flight : F->tune_G[p];
+    if (o->order < GF_ORDER_AUTO || o->order > GF_ORDER_LOCALITY) return gf_fail(GF_EINVAL, "unknown order %d", o->order);
+    x.order = o->order;
     return gf_launch_query(F, Q, m, k, p, R, warps, cps, (cudaStream_t)o->stream, ids, dists, x);
 }
 
@@ -339,13 +342,17 @@ extern "C" int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_q
     if (!o) o = &def;
     const int p = o->precision;
     if (p < 0 || p > 2) return gf_fail(GF_EINVAL, "unknown precision %d", p);
-    const int warps = o->warps_per_cta > 0 ? o->warps_per_cta : F->tune_warps[p];
+    // the streaming kernel runs at most 8 warps per CTA; fewer threads per CTA only raise the
+    // occupancy-derived grid, so the clamp keeps the size an upper bound
+    const int warps = std::min(8, o->warps_per_cta > 0 ? o->warps_per_cta : F->tune_warps[p]);
     const int cps = o->ctas_per_sm > 0 ? o->ctas_per_sm : F->tune_ctas[p];
     const int R = o->rerank_R > 0 ? o->rerank_R : F->tune_R[p];
     long long grid = 0;
     int r = gf_stream_grid(F, m, warps, cps, p, 1, R, &grid);
     if (r) return r;
-    *bytes = (int64_t)grid * ((F->n + 31) / 32) * 4;
+    const bool ordered = o->order == GF_ORDER_LOCALITY || (o->order == GF_ORDER_AUTO && m > grid);
+    const int64_t bm = (int64_t)grid * ((F->n + 31) / 32) * 4;
+    *bytes = ordered ? ((bm + 15) & ~(int64_t)15) + m * 12 + 16 : bm;
     return GF_OK;
 }
 

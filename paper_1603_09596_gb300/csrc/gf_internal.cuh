@@ -100,6 +100,7 @@ struct QueryExtra {
     int64_t workspace_bytes = 0;
     int32_t *ncand_out = nullptr;
     int32_t rows_in_flight = 0;
+    int32_t order = GF_ORDER_AUTO;
 };
 
 int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,

@@ -138,24 +138,60 @@ __device__ int gather_unique(const ForestView &F, const int *lofs, const int *lc
 
 // ---------------------------------------------------------------- scoring
 
+// Packed float32 pairs (Blackwell f32x2 instructions): each lane of a pair is rounded exactly as
+// the scalar instruction would round it, so results are bit-identical to scalar arithmetic.
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ float2 upk(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Squared-difference accumulation: a.c += (q.c - x.c)^2 for the four components, each a chain of
+// its own (the order of the terms of every chain is fixed, whichever kernel runs it).
+__device__ __forceinline__ void acc_pairs(float4 &a, unsigned long long q01, unsigned long long q23,
+                                          unsigned long long x01, unsigned long long x23) {
+    unsigned long long a01 = pk(a.x, a.y), a23 = pk(a.z, a.w);
+    const unsigned long long e01 = sub2(q01, x01), e23 = sub2(q23, x23);
+    a01 = fma2(e01, e01, a01);
+    a23 = fma2(e23, e23, a23);
+    const float2 r01 = upk(a01), r23 = upk(a23);
+    a = make_float4(r01.x, r01.y, r23.x, r23.y);
+}
+
 __device__ __forceinline__ void acc4(float4 &a, const float4 q, const float4 x) {
-    float e;
-    e = q.x - x.x; a.x = fmaf(e, e, a.x);
-    e = q.y - x.y; a.y = fmaf(e, e, a.y);
-    e = q.z - x.z; a.z = fmaf(e, e, a.z);
-    e = q.w - x.w; a.w = fmaf(e, e, a.w);
+    acc_pairs(a, pk(q.x, q.y), pk(q.z, q.w), pk(x.x, x.y), pk(x.z, x.w));
 }
 
 __device__ __forceinline__ float sum4(const float4 a) { return (a.x + a.y) + (a.z + a.w); }
 
+// a bfloat16 pair (low half first) as two floats: the bf16 bits are the float's upper 16 bits
+__device__ __forceinline__ unsigned long long bf16x2_f32x2(unsigned w) {
+    return pk(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
 // bfloat16 chunk (8 values) against 8 query floats
 __device__ __forceinline__ void acc_bf16(float4 &a, const float4 q0, const float4 q1, const uint4 c) {
-    const float2 x0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.x));
-    const float2 x1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.y));
-    const float2 x2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.z));
-    const float2 x3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&c.w));
-    acc4(a, q0, make_float4(x0.x, x0.y, x1.x, x1.y));
-    acc4(a, q1, make_float4(x2.x, x2.y, x3.x, x3.y));
+    acc_pairs(a, pk(q0.x, q0.y), pk(q0.z, q0.w), bf16x2_f32x2(c.x), bf16x2_f32x2(c.y));
+    acc_pairs(a, pk(q1.x, q1.y), pk(q1.z, q1.w), bf16x2_f32x2(c.z), bf16x2_f32x2(c.w));
 }
 
 __device__ __forceinline__ float2 e4m3x2_to_float2(unsigned short v) {
@@ -167,11 +203,14 @@ __device__ __forceinline__ float2 e4m3x2_to_float2(unsigned short v) {
 __device__ __forceinline__ void acc_fp8w(float4 &a, const float4 q, unsigned w, float s) {
     const float2 lo = e4m3x2_to_float2((unsigned short)(w & 0xffffu));
     const float2 hi = e4m3x2_to_float2((unsigned short)(w >> 16));
-    float e;
-    e = fmaf(-s, lo.x, q.x); a.x = fmaf(e, e, a.x);
-    e = fmaf(-s, lo.y, q.y); a.y = fmaf(e, e, a.y);
-    e = fmaf(-s, hi.x, q.z); a.z = fmaf(e, e, a.z);
-    e = fmaf(-s, hi.y, q.w); a.w = fmaf(e, e, a.w);
+    const unsigned long long ns = pk(-s, -s);
+    unsigned long long a01 = pk(a.x, a.y), a23 = pk(a.z, a.w);
+    const unsigned long long e01 = fma2(ns, pk(lo.x, lo.y), pk(q.x, q.y));
+    const unsigned long long e23 = fma2(ns, pk(hi.x, hi.y), pk(q.z, q.w));
+    a01 = fma2(e01, e01, a01);
+    a23 = fma2(e23, e23, a23);
+    const float2 r01 = upk(a01), r23 = upk(a23);
+    a = make_float4(r01.x, r01.y, r23.x, r23.y);
 }
 
 // Precision tags
@@ -633,7 +672,8 @@ __device__ void rescore_f32(const ForestView &F, const float *qs, const int *ids
 template <int PREC, int NC, int NCF, int G>
 __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const float *__restrict__ Q, long long m,
                                                       int k, int R, int buf_len, unsigned *bitmaps, int nwords,
-                                                      long long *ids, float *dists, int *ncand_out) {
+                                                      const int *__restrict__ order, long long *ids,
+                                                      float *dists, int *ncand_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const StreamLayout Ly = stream_layout(F.d, F.T, buf_len);
     unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem_raw + Ly.buf);
@@ -653,7 +693,8 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
     unsigned *bm = bitmaps + (size_t)blockIdx.x * nwords;
     const unsigned lt = (1u << lane) - 1u;
 
-    for (long long qi = blockIdx.x; qi < m; qi += gridDim.x) {
+    for (long long qs_i = blockIdx.x; qs_i < m; qs_i += gridDim.x) {
+        const long long qi = order ? (long long)order[qs_i] : qs_i;  // CTAs walk the batch in `order`
         load_query(Q + qi * F.d, F.d, qs);
         __syncthreads();
         for (int t = threadIdx.x; t < F.T; t += blockDim.x)
@@ -745,6 +786,33 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
         if (threadIdx.x == 0 && ncand_out) ncand_out[qi] = sh[3];
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------- query order (locality)
+//
+// Queries that reach the same leaf of tree 0 share most of their candidates, so a batch walked in
+// order of that leaf lets CTAs running at the same time read the same rows (from L2).  The order
+// changes no result: every query's answer is computed on its own.
+
+constexpr int ORDER_CHUNK = 16384;  // queries sorted together by one CTA
+
+__global__ void k_order_keys(ForestView F, const float *__restrict__ Q, long long m, unsigned long long *keys) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int leaf0 = descend_tree(F.nodes, F.L, Q + i * F.d);
+    keys[i] = ((unsigned long long)(unsigned)leaf0 << 32) | (unsigned long long)(i & 0xffffffffll);
+}
+
+__global__ void k_order_sort(long long m, const unsigned long long *__restrict__ keys, int *order) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *k = reinterpret_cast<unsigned long long *>(smem_raw);
+    const long long base = (long long)blockIdx.x * ORDER_CHUNK;
+    const int cnt = (int)min((long long)ORDER_CHUNK, m - base);
+    int P = 1;
+    while (P < cnt) P <<= 1;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) k[j] = j < cnt ? keys[base + j] : KEY_NONE;
+    block_sort<unsigned long long>(k, P);
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) order[base + j] = (int)(unsigned)(k[j] & 0xffffffffu);
 }
 
 // ---------------------------------------------------------------- host side
@@ -841,7 +909,9 @@ int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         return GF_OK;
     }
     const int nwords = (int)((F->n + 31) / 32);
-    const size_t ws_bytes = (size_t)grid * nwords * 4;
+    const bool ordered = x.order == GF_ORDER_LOCALITY || (x.order == GF_ORDER_AUTO && m > grid);
+    const size_t bm_bytes = (size_t)grid * nwords * 4;
+    const size_t ws_bytes = bm_bytes + (ordered ? (size_t)m * 12 + 16 : 0);
     unsigned *bitmaps = (unsigned *)x.workspace;
     bool own = false;
     if (bitmaps) {
@@ -857,7 +927,22 @@ int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         e = cudaMemsetAsync(bitmaps, 0, ws_bytes, st);
         if (e != cudaSuccess) { cudaFreeAsync(bitmaps, st); return gf_cuda_fail(e, "workspace memset"); }
     }
-    kern<<<(unsigned)grid, threads, smem, st>>>(view_of(F), Q, m, k, R, buf_len, bitmaps, nwords,
+    int *order = nullptr;
+    if (ordered) {
+        // keys (8 B) then order (4 B) per query, after the bitmaps (16-byte aligned)
+        unsigned long long *okeys = (unsigned long long *)((char *)bitmaps + ((bm_bytes + 15) & ~(size_t)15));
+        order = (int *)(okeys + m);
+        k_order_keys<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(view_of(F), Q, m, okeys);
+        const long long chunks = (m + ORDER_CHUNK - 1) / ORDER_CHUNK;
+        const int P = next_pow2((int)std::min<long long>(m, ORDER_CHUNK));
+        const size_t osmem = (size_t)P * 8;
+        if ((r = prep_kernel(k_order_sort, osmem))) {
+            if (own) cudaFreeAsync(bitmaps, st);
+            return r;
+        }
+        k_order_sort<<<(unsigned)chunks, 1024, osmem, st>>>(m, okeys, order);
+    }
+    kern<<<(unsigned)grid, threads, smem, st>>>(view_of(F), Q, m, k, R, buf_len, bitmaps, nwords, order,
                                                (long long *)ids, dists, x.ncand_out);
     cudaError_t e = cudaGetLastError();
     if (own) cudaFreeAsync(bitmaps, st);

@@ -32,13 +32,14 @@ class RandParams(C.Structure):
 
 
 GF_ALGO_AUTO, GF_ALGO_SORT, GF_ALGO_STREAM = 0, 1, 2
+GF_ORDER_AUTO, GF_ORDER_GIVEN, GF_ORDER_LOCALITY = 0, 1, 2
 
 
 class QueryOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rerank_R", C.c_int32), ("warps_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("stream", C.c_void_p), ("algo", C.c_int32),
                 ("rows_in_flight", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64),
-                ("ncand_out", C.c_void_p)]
+                ("ncand_out", C.c_void_p), ("order", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ServerOpts(C.Structure):
@@ -212,9 +213,9 @@ def gf_forest_set_tuning(F: Forest, precision: int, warps_per_cta: int, ctas_per
 
 
 def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
-          rows_in_flight=0):
+          rows_in_flight=0, order=GF_ORDER_AUTO):
     o = QueryOpts(precision, rerank_R, warps_per_cta, ctas_per_sm, _stream(stream), algo, rows_in_flight,
-                  None, 0, None)
+                  None, 0, None, order, 0)
     if workspace is not None:
         o.workspace = _dptr(workspace, workspace.dtype, "workspace")
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -226,7 +227,8 @@ def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspa
 def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, rerank_R: int = 0,
              warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None, algo: int = GF_ALGO_AUTO,
              workspace: torch.Tensor | None = None, ncand_out: torch.Tensor | None = None,
-             rows_in_flight: int = 0, out: tuple[torch.Tensor, torch.Tensor] | None = None):
+             rows_in_flight: int = 0, order: int = GF_ORDER_AUTO,
+             out: tuple[torch.Tensor, torch.Tensor] | None = None):
     """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k])."""
     m = Q.shape[0]
     if out is None:
@@ -235,15 +237,15 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
     else:
         ids, dists = out
     o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
-              rows_in_flight)
+              rows_in_flight, order)
     _check(lib().gf_query_ex(F.handle, _dptr(Q, torch.float32, "Q"), m, k, C.byref(o),
                              _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists")))
     return ids, dists
 
 
 def gf_query_workspace_size(F: Forest, m: int, precision: int = GF_FP32, rerank_R: int = 0,
-                            warps_per_cta: int = 0, ctas_per_sm: int = 0) -> int:
-    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, None, GF_ALGO_STREAM, None, None)
+                            warps_per_cta: int = 0, ctas_per_sm: int = 0, order: int = GF_ORDER_AUTO) -> int:
+    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, None, GF_ALGO_STREAM, None, None, 0, order)
     b = C.c_int64()
     _check(lib().gf_query_workspace_size(F.handle, m, C.byref(o), C.byref(b)))
     return b.value

@@ -2,7 +2,8 @@
 
 With the same data, parameters and seed both sides make the same random draws, so the forests
 must agree node for node; the only admissible difference is a near-tie in the variance ranking
-(float64 sums on the GPU, Welford's recurrence in the oracle), which is checked explicitly.  Every
+(compensated float32 sums combined in float64 on the GPU, Welford's float64 recurrence in the
+oracle; both within 1e-10 relative of the exact variance), which is checked explicitly.  Every
 GPU forest must also satisfy the partition invariants on its own.
 """
 import numpy as np
@@ -58,7 +59,8 @@ def assert_same_forest(X, Fg, Fo, t):
         var = oracle.variance(X, np.sort(pts).astype(np.int32))
         sg, so = Fg.split_dim[tr, j], Fo.split_dim[tr, j]
         order = np.lexsort((np.arange(len(var)), -var))
-        near = np.abs(var - var[order[t - 1]]) <= 1e-12 * abs(var[order[t - 1]]) + 1e-300
+        # the GPU's compensated float32 sums are within ~cnt * 2^-48 (< 1e-10) of float64
+        near = np.abs(var - var[order[t - 1]]) <= 1e-10 * abs(var[order[t - 1]]) + 1e-300
         assert near.sum() > 1 or sg == so, f"tree {tr} node {j}: GPU split {sg}, oracle {so}, no variance tie"
     assert len(first_divergence(Fg, Fo)) <= max(1, Fo.T // 8)
 

@@ -313,3 +313,25 @@ def test_stream_large_screened(gf, prec, R):
     offs, ids = oracle.candidates(F, oracle.descend(F, Q))
     oi, od, _ = screen.screened_search(F, X, Q, 10, R, prec, offs, ids)
     assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_locality_order_changes_no_result(gf, prec):
+    # CTAs taking the queries sorted by their tree-0 leaf: every answer (and candidate count) stays
+    # at its query's row and is bit-identical to the batch taken as given
+    X, Q, F = case("gist_like")
+    G, _ = gpu_forest(gf, X, F)
+    p = gf.PRECISIONS[prec]
+    if p:
+        gf.gf_forest_add_screen(G, p)
+    Qg = torch.from_numpy(Q).cuda()
+    res = {}
+    for order in (gf.GF_ORDER_GIVEN, gf.GF_ORDER_LOCALITY, gf.GF_ORDER_AUTO):
+        nc = torch.full((Q.shape[0],), -1, dtype=torch.int32, device="cuda")
+        i, d = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_STREAM, ctas_per_sm=1,
+                           order=order, ncand_out=nc)
+        res[order] = (i, d, nc)
+    a = res[gf.GF_ORDER_GIVEN]
+    for order in (gf.GF_ORDER_LOCALITY, gf.GF_ORDER_AUTO):
+        b = res[order]
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
