@@ -428,6 +428,42 @@ def highd(args):
                       "cand_per_query": round(C, 1), "build_s": round(build_s, 2), "results": out}))
 
 
+def klein(args):
+    """Low-intrinsic-dimension workload: a noisy Klein bottle in R^100 (the paper's Klein set, Sec. 4,
+    at 10^6 points), one leaf per tree; recall and the epsilon-miss rate of Sec. 4."""
+    import torch
+    import paper_1603_09596_gb300 as gf
+    from paper_1603_09596_gb300 import autotune
+    import synth
+    n, d, m, T, p, k = 1_000_000, 100, 10_000, 32, 64, 10
+    X, Q = synth.manifold(n, d, m, "klein", seed=0, qseed=1)
+    dev = torch.device("cuda", 0)
+    Xg, Qg = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    S = min(m, args.recall_sample)
+    ei, ed = exact_nn(torch, Xg, Qg[:S], k)
+    tb = time.time()
+    F = gf.gf_build(Xg, T, p, seed=0)
+    torch.cuda.synchronize()
+    build_s = time.time() - tb
+    gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
+    out = {}
+    for name in ("fp32", "bf16"):
+        prec = gf.PRECISIONS[name]
+        tr = autotune.tune(F, Qg[:min(m, 2000)], k, prec)
+        ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, no_graph=args.no_graph)
+        r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
+        got = Xg[ids[:S, 0].clamp(min=0)].double()
+        dr = ((got - Qg[:S].double()) ** 2).sum(1).sqrt()
+        de = ed[:, 0].sqrt()
+        eps_miss = {str(e): float(((dr > (1 + e) * de) | (ids[:S, 0] < 0)).double().mean()) for e in (0.0, 0.1, 0.5, 0.9)}
+        mean_ms = statistics.mean(ms)
+        out[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4), "recall_at_1": r1,
+                     "recall_at_10": rk, "eps_miss": eps_miss, "R": tr.get("R", 0), "clocks": ck}
+    print(json.dumps({"metric": "queries/s, noisy Klein bottle in R^100, n=10^6, k=10", "unit": "queries/s",
+                      "n": n, "d": d, "m": m, "T": T, "leaf_size": p, "build_s": round(build_s, 2),
+                      "results": out}))
+
+
 SERVE_FORESTS = [  # (n, d, T, leaf_size): six resident forests of uneven size
     (10_000, 128, 16, 256), (50_000, 512, 16, 256), (100_000, 960, 24, 256),
     (500_000, 960, 32, 512), (1_000_000, 960, 32, 1024), (100_000, 4096, 16, 256)]
@@ -532,6 +568,7 @@ def main():
     ap.add_argument("--profile-ctas", type=int, default=0)
     ap.add_argument("--serve", action="store_true", help="serving workload (six forests, Poisson load)")
     ap.add_argument("--highd", action="store_true", help="d = 10^4 workload: fp8 / bf16 / fp32")
+    ap.add_argument("--klein", action="store_true", help="noisy Klein bottle in R^100, 10^6 points")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB for batch slots")
@@ -542,6 +579,8 @@ def main():
         serve(args)
     elif args.highd:
         highd(args)
+    elif args.klein:
+        klein(args)
     elif args.impl == "reference":
         reference(args)
     else:

@@ -26,7 +26,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Law", "LAWS", "mixture", "quantize_u8", "BLOCK_ROWS"]
+__all__ = ["Law", "LAWS", "mixture", "manifold", "quantize_u8", "BLOCK_ROWS"]
 
 BLOCK_ROWS = 16384
 
@@ -100,6 +100,50 @@ def mixture(n: int, d: int, m: int, law: str = "A", seed: int = 0, qseed: int = 
         X -= mn
         Q -= mn
     return X, Q
+
+
+def _frame(k: int, d: int, seed: int) -> np.ndarray:
+    """A seeded random orthonormal k x d frame (rows orthonormal), k <= d."""
+    rng = np.random.default_rng([seed, 0xF0])
+    G = rng.standard_normal((d, k))
+    Qm, R = np.linalg.qr(G)
+    return (Qm * np.sign(np.diag(R))).T  # k x d
+
+
+def _manifold_points(kind: str, count: int, rng) -> np.ndarray:
+    if kind == "klein":
+        # the Klein bottle's embedding in R^4 with radii 2 and 1:
+        # ((2 + cos v) cos u, (2 + cos v) sin u, sin v cos(u/2), sin v sin(u/2)), u, v uniform
+        u = rng.uniform(0, 2 * np.pi, count)
+        v = rng.uniform(0, 2 * np.pi, count)
+        return np.stack([(2 + np.cos(v)) * np.cos(u), (2 + np.cos(v)) * np.sin(u),
+                         np.sin(v) * np.cos(u / 2), np.sin(v) * np.sin(u / 2)], axis=1)
+    if kind == "sphere":
+        # uniform on the unit 2-sphere
+        g = rng.standard_normal((count, 3))
+        return g / np.linalg.norm(g, axis=1, keepdims=True)
+    raise ValueError(kind)
+
+
+def manifold(n: int, d: int, m: int, kind: str = "klein", noise: float | None = None, seed: int = 0,
+             qseed: int = 1) -> tuple[np.ndarray, np.ndarray]:
+    """Noisy low-dimensional manifold in R^d (the paper's Klein-bottle and sphere sets, Sec. 4).
+
+    Points are drawn uniformly in the manifold's parameters, mapped into R^d by a seeded random
+    orthonormal frame, and every coordinate gets N(0, noise^2) (0.05 for the Klein bottle, 0.1 for
+    the sphere, as in the paper).  Queries are independent draws from the same law.
+    """
+    if noise is None:
+        noise = 0.05 if kind == "klein" else 0.1
+    dim = 4 if kind == "klein" else 3
+    Fr = _frame(dim, d, seed)
+    out = []
+    for cnt, sd in ((n, [seed, 11]), (m, [qseed, 12])):
+        rng = np.random.default_rng(sd)
+        P = _manifold_points(kind, cnt, rng) @ Fr
+        P += rng.standard_normal(P.shape) * noise
+        out.append(P.astype(np.float32))
+    return out[0], out[1]
 
 
 def quantize_u8(A: np.ndarray, scale: float = 8.0) -> np.ndarray:

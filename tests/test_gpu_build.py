@@ -78,9 +78,12 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("n,d,T,p,law,t,shuffle,scope", CASES)
+@pytest.mark.parametrize("n,d,T,p,law,t,shuffle,scope", CASES + [(12_000, 100, 4, 32, "klein", 5, 1, 0)])
 def test_build_matches_oracle(gf, n, d, T, p, law, t, shuffle, scope):
-    X, _ = synth.mixture(n, d, 1, law, seed=n)
+    if law == "klein":
+        X, _ = synth.manifold(n, d, 1, "klein", seed=n)
+    else:
+        X, _ = synth.mixture(n, d, 1, law, seed=n)
     G, Fg = gpu_build(gf, X, T, p, t=t, shuffle=shuffle, var_scope=scope, seed=3)
     Fo = oracle.build_forest(X, T, p, t=t, shuffle=shuffle, var_scope=scope, seed=3)
     assert_same_forest(X, Fg, Fo, t)

@@ -16,14 +16,15 @@ from parity import RTOL, assert_topk_close, candidate_sets
 pytestmark = pytest.mark.gpu
 
 # (name, n, d, m, T, leaf_size, law): the tiny workload, ragged sizes (d not a multiple of 4/8/16,
-# m and n odd), more trees than a warp, a row longer than the register-resident query, and the
-# 960-d GIST-like law.
+# m and n odd), more trees than a warp, a row longer than the register-resident query, the
+# 960-d GIST-like law, and a noisy Klein bottle in R^100 (low intrinsic dimension).
 CASES = [
     ("tiny", 10_000, 128, 100, 8, 32, "A"),
     ("ragged", 3001, 37, 57, 5, 9, "B"),
     ("manytrees", 5000, 64, 40, 40, 16, "A"),
     ("long_rows", 3000, 2000, 30, 6, 40, "C"),
     ("gist_like", 20_000, 960, 200, 16, 64, "B"),
+    ("klein", 10_000, 100, 100, 8, 32, "klein"),   # the paper's Klein-bottle set (Sec. 4)
 ]
 
 
@@ -41,7 +42,10 @@ def case(name):
     if name not in _cache:
         spec = next(c for c in CASES if c[0] == name)
         _, n, d, m, T, p, law = spec
-        X, Q = synth.mixture(n, d, m, law, seed=0, qseed=1)
+        if law in ("klein", "sphere"):
+            X, Q = synth.manifold(n, d, m, law, seed=0, qseed=1)
+        else:
+            X, Q = synth.mixture(n, d, m, law, seed=0, qseed=1)
         F = oracle.build_forest(X, T, p, t=min(5, d), seed=7)
         _cache[name] = (X, Q, F)
     return _cache[name]
