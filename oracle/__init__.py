@@ -58,7 +58,7 @@ def lib():
         L.gfo_search.restype = None
         L.gfo_bruteforce.argtypes = [P, i64, i32, P, i64, i32, P, P]; L.gfo_bruteforce.restype = None
         L.gfo_search_priority.argtypes = [P, i64, i32, P, P, P, i32, i32, P, i64, i32, i64, C.c_double,
-                                          P, P, P, P]
+                                          P, P, P, P, P, i64]
         L.gfo_search_priority.restype = None
         L.gfo_num_threads.argtypes = []; L.gfo_num_threads.restype = i32
         _lib = L
@@ -202,19 +202,23 @@ def search(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, return_ncand: bool =
     return (oi, od, nc) if return_ncand else (oi, od)
 
 
-def search_priority(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, c: int, eps: float = 0.0):
+def search_priority(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, c: int, eps: float = 0.0,
+                    return_leaves: bool = False):
     """Alg. 2 with the shared priority queue: at least the T first leaves, then leaves in order of
-    |q_s - v| until c / (1 + eps) were checked.  Returns ids, dists, candidates, leaves checked."""
+    |q_s - v| until c / (1 + eps) were checked.  Returns ids, dists, candidates, leaves checked (and
+    with return_leaves the leaf sequence, (tree << L) | leaf, -1 padded)."""
     X, Q = _f32(X), _f32(Q)
     m = Q.shape[0]
     oi = np.empty((m, k), dtype=np.int64)
     od = np.empty((m, k), dtype=np.float64)
     nc = np.empty(m, dtype=np.int64)
     nl = np.empty(m, dtype=np.int64)
+    cap = max(int(c / (1.0 + eps)) + 1, F.T)
+    seq = np.full((m, cap), -1, dtype=np.int64)
     lib().gfo_search_priority(_p(X), F.n, F.d, _p(np.ascontiguousarray(F.split_dim)),
                               _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
-                              F.L, F.T, _p(Q), m, k, c, eps, _p(oi), _p(od), _p(nc), _p(nl))
-    return oi, od, nc, nl
+                              F.L, F.T, _p(Q), m, k, c, eps, _p(oi), _p(od), _p(nc), _p(nl), _p(seq), cap)
+    return (oi, od, nc, nl, seq) if return_leaves else (oi, od, nc, nl)
 
 
 def bruteforce(X: np.ndarray, Q: np.ndarray, k: int):

@@ -432,6 +432,7 @@ void gfo_search(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
  * k-best list H.  Reading R8: the first descent of every tree checks its leaf too and counts as a
  * checked leaf (with c = T the search is exactly R7); afterwards nodes are extracted from Q in
  * order of (key, tree, node) and descended while fewer than c / (1 + eps) leaves were checked.
+ * If leaf_seq is not NULL, row i receives the first seq_cap leaves checked, as (tree << L) | leaf.
  */
 typedef struct {
     double key;
@@ -486,7 +487,8 @@ static void kbest_insert(kbest_t *H, res_t r) {
 void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
                          const float *split_val, const int32_t *perm, int32_t L, int32_t T,
                          const float *Q, int64_t m, int32_t k, int64_t c, double eps,
-                         int64_t *out_ids, double *out_d, int64_t *ncand, int64_t *nleaves) {
+                         int64_t *out_ids, double *out_d, int64_t *ncand, int64_t *nleaves,
+                         int64_t *leaf_seq, int64_t seq_cap) {
     int64_t nn = ((int64_t)1 << L) - 1;
     double budget = (double)c / (1.0 + eps);
 #pragma omp parallel
@@ -505,22 +507,25 @@ void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *sp
             /* one descent from node j of tree t to a leaf, pushing the siblings, checking the leaf */
 #define GFO_DESCEND(t_, j_)                                                                        \
             do {                                                                                   \
+                const int32_t tree_ = (t_);   /* arguments evaluated once, before any push */     \
                 int64_t j = (j_);                                                                  \
-                const int32_t *sd = split_dim + (int64_t)(t_) * nn;                                \
-                const float *sv = split_val + (int64_t)(t_) * nn;                                  \
+                const int32_t *sd = split_dim + (int64_t)tree_ * nn;                               \
+                const float *sv = split_val + (int64_t)tree_ * nn;                                 \
                 while (j < nn) {                                                                   \
                     double dd = (double)q[sd[j]] - (double)sv[j];                                  \
-                    qent_t e;                                                                      \
-                    e.key = fabs(dd);                                                              \
-                    e.tree = (t_);                                                                 \
-                    if (q[sd[j]] < sv[j]) { e.node = 2 * j + 2; j = 2 * j + 1; }                   \
-                    else { e.node = 2 * j + 1; j = 2 * j + 2; }                                    \
-                    heap_push(heap, &hs, e);                                                       \
+                    qent_t pushed_;                                                                \
+                    pushed_.key = fabs(dd);                                                        \
+                    pushed_.tree = tree_;                                                          \
+                    if (q[sd[j]] < sv[j]) { pushed_.node = 2 * j + 2; j = 2 * j + 1; }             \
+                    else { pushed_.node = 2 * j + 1; j = 2 * j + 2; }                              \
+                    heap_push(heap, &hs, pushed_);                                                 \
                 }                                                                                  \
                 int64_t b = j - nn;                                                                \
+                if (leaf_seq && checked < seq_cap)                                                 \
+                    leaf_seq[i * seq_cap + checked] = ((int64_t)tree_ << L) | b;                   \
                 int64_t lo = pos_of(n, L, b), hi = pos_of(n, L, b + 1);                            \
                 for (int64_t p = lo; p < hi; p++) {                                                \
-                    int32_t id = perm[(int64_t)(t_) * n + p];                                      \
+                    int32_t id = perm[(int64_t)tree_ * n + p];                                     \
                     if (seen[id]) continue;                                                        \
                     seen[id] = 1;                                                                  \
                     if (ntouch == tcap) {                                                          \
@@ -537,8 +542,8 @@ void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *sp
             for (int32_t t = 0; t < T; t++) GFO_DESCEND(t, 0);
             while (hs > 0 && (double)checked < budget) {
                 if (hs + L + 1 > hcap) break;
-                qent_t e = heap_pop(heap, &hs);
-                GFO_DESCEND(e.tree, e.node);
+                const qent_t top = heap_pop(heap, &hs);
+                GFO_DESCEND(top.tree, top.node);
             }
 #undef GFO_DESCEND
             for (int32_t j = 0; j < k; j++) {

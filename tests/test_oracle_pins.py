@@ -329,3 +329,17 @@ def test_priority_search_budget_and_monotonicity():
     # c / (1 + eps) leaves: eps = 1 halves the budget (Sec. 2.3)
     _, _, _, nl = oracle.search_priority(F, X, Q, 1, 40, eps=1.0)
     assert np.all(nl == 20)
+
+
+def test_priority_pop_order_across_trees(golden_dir):
+    # a hand-made two-tree forest: the queue mixes both trees and breaks a key tie by tree
+    g = json.load(open(os.path.join(golden_dir, "hand_prio_2trees.json")))
+    X = np.array(g["X"], dtype=np.float32)
+    F = oracle.Forest(8, 2, 2, 2, g["L"], np.array(g["split_dim"], dtype=np.int32),
+                      np.array(g["split_val"], dtype=np.float32), np.array(g["perm"], dtype=np.int32))
+    q = np.array([g["query"]], dtype=np.float32)
+    _, _, nc, nl, seq = oracle.search_priority(F, X, q, 1, 8, return_leaves=True)
+    assert seq[0, :8].tolist() == g["sequence"]
+    for c, cand in g["candidates_after_c"].items():
+        _, _, nc, nl = oracle.search_priority(F, X, q, 1, int(c))
+        assert (nl[0], nc[0]) == (int(c), cand)
