@@ -91,7 +91,9 @@ typedef struct gf_query_opts {
     int32_t *ncand_out;      /* STREAM only, optional: device [m] int32, number of distinct
                                 candidates of each query */
     int32_t order;           /* STREAM only, GF_ORDER_*: the order in which CTAs take queries */
-    int32_t reserved;
+    int32_t checks;          /* the paper's c, max. leaf checks (Alg. 2, Sec. 3 "Parameters");
+                                <= T: one leaf per tree (the default search) */
+    double eps;              /* the paper's epsilon >= 0: c / (1 + eps) leaves are checked */
 } gf_query_opts;
 
 typedef struct gf_forest gf_forest; /* opaque; owned by the library */
@@ -182,6 +184,10 @@ int gf_forest_free(gf_forest *F);
  *   ids    device [m][k] int64: point ids ordered by (distance, id); -1 where a query has fewer
  *          than k candidates
  *   dists  device [m][k] float32: squared L2 distances (float32 arithmetic); +inf with id -1
+ * With opts.checks = c > T (gf_query_ex) the search is Alg. 2 with the shared priority queue: after
+ * the first leaf of every tree, nodes are taken from one queue over all trees in order of
+ * (|q_s - v|, tree, node) and descended, until max(T, ceil(c / (1 + eps))) leaves were checked;
+ * the points of all checked leaves are the candidates (at most 4096 leaves; needs T * 2^L <= 2^32).
  * Precision GF_FP32 on the legacy default stream.  m = 0 is a no-op.  Queries containing NaN give
  * unspecified ids but never read or write out of bounds.  The streaming kernel allocates its
  * scratch stream-ordered unless gf_query_ex is given a workspace.
@@ -326,6 +332,15 @@ int gf_server_run_poisson(gf_server *S, const float *const *queries_host, const 
 
 /* Stop the threads after the batches in flight finish, free the slots.  Pending tickets die. */
 int gf_server_destroy(gf_server *S);
+
+/* The leaves Alg. 2's priority search checks for each query (the first step of gf_query_ex with
+ * opts.checks = c), in the order it checks them: the first leaf of every tree, then leaves taken
+ * from the shared queue by (|q_s - v|, tree, node).  leaves: device [m][stride] uint32, each
+ * (tree << L) | leaf; nleaves: device [m] int32, the number checked (fewer than stride only when
+ * the queue runs dry).  stride must equal the leaf budget max(T, ceil(c / (1 + eps))) (<= 4096).
+ * Errors: GF_EINVAL, GF_EUNSUPPORTED (T * 2^L > 2^32, budget above 4096). */
+int gf_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int32_t checks, double eps,
+                   uint32_t *leaves, int32_t *nleaves, int32_t stride, void *stream);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -74,3 +74,46 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
     gf.gf_forest_set_tuning(F, precision, w, c, R, g)
     _cache[key] = res
     return res
+
+
+# ---------------------------------------------------------------- forest configuration
+#
+# Sec. 3 ("Configuration") sets the leaf size p, the leaf checks c, the split-dimension count t and
+# the number of trees from (epsilon, n, d, the top-5 variances) with piecewise-constant rules whose
+# constants the paper does not print.  configure() is the hook in their place: it measures.  For a
+# grid of (T, leaf_size, c) it builds the forest on the GPU, runs the query sample, and scores
+# recall@1 against the exact nearest neighbours -- computed by this library itself on a one-leaf
+# forest (leaf_size >= n makes every query scan all points exactly).  It returns the fastest
+# configuration whose recall@1 reaches the target.
+
+DEFAULT_GRID = [(T, p, c) for T in (16, 32) for p in (64, 256, 1024) for c in (0,)]
+
+
+def exact_neighbours(X: torch.Tensor, Q: torch.Tensor, k: int = 1):
+    """Exact k-NN by the library's own kernel: one tree whose single leaf holds every point."""
+    F1 = gf.gf_build(X, 1, X.shape[0], seed=0)
+    ids, d = gf.gf_query(F1, Q, k, algo=gf.GF_ALGO_STREAM)
+    torch.cuda.synchronize()
+    F1.free()
+    return ids, d
+
+
+def recall_at_1(F: gf.Forest, Q: torch.Tensor, exact_d: torch.Tensor, checks: int = 0) -> float:
+    ids, d = gf.gf_query(F, Q, 1, checks=checks)
+    return float((d[:, 0] <= exact_d[:, 0]).float().mean())
+
+
+def configure(X: torch.Tensor, Q: torch.Tensor, target_recall: float = 0.9, grid=DEFAULT_GRID,
+              t: int = 5, seed: int = 0) -> dict:
+    """Fastest (T, leaf_size, checks) on the grid whose recall@1 on Q reaches target_recall."""
+    _, ed = exact_neighbours(X, Q)
+    tried = []
+    for T, p, c in grid:
+        F = gf.gf_build(X, T, p, t=min(t, X.shape[1]), seed=seed)
+        r = recall_at_1(F, Q, ed, checks=c)
+        ms = _time(lambda: gf.gf_query(F, Q, 10, checks=c))
+        tried.append({"T": T, "leaf_size": p, "checks": c, "recall_at_1": r, "ms": ms})
+        F.free()
+    ok = [e for e in tried if e["recall_at_1"] >= target_recall]
+    best = min(ok, key=lambda e: e["ms"]) if ok else max(tried, key=lambda e: e["recall_at_1"])
+    return {"choice": best, "met_target": bool(ok), "tried": tried}

@@ -329,6 +329,13 @@ extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_
     x.rows_in_flight = o->rows_in_flight > 0 ? o->rows_in_flight : F->tune_G[p];
     if (o->order < GF_ORDER_AUTO || o->order > GF_ORDER_LOCALITY) return gf_fail(GF_EINVAL, "unknown order %d", o->order);
     x.order = o->order;
+    if (o->checks < 0 || !(o->eps >= 0.0)) return gf_fail(GF_EINVAL, "checks < 0 or eps < 0");
+    x.leaf_budget = leaf_budget_of(F, o->checks, o->eps);
+    if (x.leaf_budget > 0) {
+        if (((unsigned long long)F->T << F->L) > 0xffffffffull)
+            return gf_fail(GF_EUNSUPPORTED, "priority search needs T * 2^L <= 2^32");
+        if (x.leaf_budget > 4096) return gf_fail(GF_EUNSUPPORTED, "leaf budget %d above 4096", x.leaf_budget);
+    }
     return gf_launch_query(F, Q, m, k, p, R, warps, cps, (cudaStream_t)o->stream, ids, dists, x);
 }
 
@@ -351,9 +358,7 @@ extern "C" int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_q
     int r = gf_stream_grid(F, m, warps, cps, p, 1, R, &grid);
     if (r) return r;
     const bool ordered = o->order == GF_ORDER_LOCALITY || (o->order == GF_ORDER_AUTO && m > grid);
-    const int64_t bm = (int64_t)grid * ((F->n + 31) / 32) * 4;
-    *bytes = ordered ? ((bm + 15) & ~(int64_t)15) + m * 12 + 16 : bm;
-    return GF_OK;
+    return gf_stream_workspace_bytes(F, m, grid, ordered, leaf_budget_of(F, o->checks, o->eps), bytes);
 }
 
 extern "C" int gf_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int64_t *ids,

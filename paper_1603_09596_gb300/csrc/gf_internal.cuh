@@ -101,7 +101,23 @@ struct QueryExtra {
     int32_t *ncand_out = nullptr;
     int32_t rows_in_flight = 0;
     int32_t order = GF_ORDER_AUTO;
+    int32_t leaf_budget = 0;  // leaves per query for the priority search (0: one per tree)
 };
+
+int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int budget, unsigned *leaves,
+                          int *nleaves, cudaStream_t st);
+size_t gf_prio_smem_bytes(int budget);
+int gf_stream_workspace_bytes(const gf_forest *F, int64_t m, long long grid, bool ordered, int leaf_budget,
+                              int64_t *bytes);
+
+// Leaves the priority search checks per query: max(T, ceil(checks / (1 + eps))), 0 when that is T.
+inline int32_t leaf_budget_of(const gf_forest *F, int32_t checks, double eps) {
+    if (checks <= F->T) return 0;
+    const double budget = (double)checks / (1.0 + eps);
+    long long nl = F->T;
+    while ((double)nl < budget) ++nl;  // the same comparison the search loop makes
+    return nl > F->T ? (int32_t)nl : 0;
+}
 
 int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,
                     int32_t R, int32_t warps, int32_t ctas_per_sm, cudaStream_t s, int64_t *ids,

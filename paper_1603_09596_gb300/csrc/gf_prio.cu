@@ -1,0 +1,200 @@
+// gf_prio.cu -- the leaves a query checks under Alg. 2's shared priority queue (Sec. 2.3).
+//
+// For each query, in the order of Alg. 2:
+//   * every tree is descended from its root (Eq. 1); each node passed pushes the child not taken
+//     with key |q_s - v|; the leaf reached is checked (reading: these first T leaves count toward
+//     the budget, so a budget of T leaves is exactly the one-leaf-per-tree search);
+//   * then, while fewer than `budget` leaves were checked, the entry of smallest
+//     (key, tree, node) is taken from the queue and descended the same way to one more leaf.
+// The keys are computed in float64 (the difference of two floats is exact there), so the order,
+// including ties, is exactly the CPU oracle's.
+//
+// One warp per query.  The queue is a sorted array in shared memory; the entries a descent pushes
+// (at most L <= 30, or one per tree in the first phase) are merged into it by the warp.  Entries
+// ranked beyond the number of pops still to come can never be taken and are dropped, so the array
+// never holds more than `budget` + 32 entries.  The output is the list of leaves in the order
+// checked, encoded (tree << L) | leaf.
+#include "gf_internal.cuh"
+
+#include <algorithm>
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int PRIO_WARPS = 4;  // at most this many warps (queries) per CTA
+
+struct PQE {
+    double key;
+    int tree;
+    int node;
+};
+
+__device__ __forceinline__ bool pq_less(const PQE &a, const PQE &b) {
+    if (a.key != b.key) return a.key < b.key;
+    if (a.tree != b.tree) return a.tree < b.tree;
+    return a.node < b.node;
+}
+
+__device__ __forceinline__ PQE pq_inf() {
+    PQE e;
+    e.key = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+    e.tree = 0x7fffffff;
+    e.node = 0x7fffffff;
+    return e;
+}
+
+// Merge the nb (<= 32) entries of stage[] into the sorted array src[0..cnt); write the first
+// min(cnt + nb, keep) entries of the merged order to dst[]; returns their number.  Warp-wide.
+__device__ int pq_merge(const PQE *src, int cnt, PQE *stage, int nb, PQE *dst, int keep, PQE *sorted) {
+    const int lane = threadIdx.x & 31;
+    // rank of every staged entry among the staged entries (all distinct)
+    PQE mine = lane < nb ? stage[lane] : pq_inf();
+    int r = 0;
+    for (int i = 0; i < nb; ++i) r += pq_less(stage[i], mine);
+    __syncwarp();
+    if (lane < nb) sorted[r] = mine;
+    __syncwarp();
+    // staged entry r goes to r + (number of src entries below it)
+    if (lane < nb) {
+        int lo = 0, hi = cnt;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (pq_less(src[mid], mine)) lo = mid + 1;
+            else hi = mid;
+        }
+        const int pos = r + lo;
+        if (pos < keep) dst[pos] = mine;
+    }
+    // src entry j goes to j + (number of staged entries below it)
+    for (int j = lane; j < cnt; j += 32) {
+        const PQE e = src[j];
+        int lo = 0, hi = nb;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (pq_less(sorted[mid], e)) lo = mid + 1;
+            else hi = mid;
+        }
+        const int pos = j + lo;
+        if (pos < keep) dst[pos] = e;
+    }
+    __syncwarp();
+    return min(cnt + nb, keep);
+}
+
+__device__ __forceinline__ unsigned leaf_code(int tree, int leaf, int L) {
+    return ((unsigned)tree << L) | (unsigned)leaf;
+}
+
+__global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, const float *__restrict__ Q,
+                                                                long long m, int budget, int cap,
+                                                                unsigned *leaves, int *nleaves) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // per warp: two queue arrays of `cap` entries, the staged batch and its sorted copy
+    PQE *base = reinterpret_cast<PQE *>(smem_raw) + (size_t)w * (2 * cap + 64);
+    PQE *qa = base, *qb = base + cap, *stage = base + 2 * cap, *sorted = stage + 32;
+    const int nn = (1 << F.L) - 1;
+    const int nwq = blockDim.x >> 5;
+    for (long long qi = (long long)blockIdx.x * nwq + w; qi < m; qi += (long long)gridDim.x * nwq) {
+        const float *q = Q + qi * F.d;
+        unsigned *out = leaves + qi * budget;
+        int cnt = 0, head = 0, checked = 0;
+        // ---- first descent of every tree, 32 trees at a time, one level per merge
+        for (int t0 = 0; t0 < F.T; t0 += 32) {
+            const int t = t0 + lane;
+            const bool act = t < F.T;
+            int j = 0;
+            for (int l = 0; l < F.L; ++l) {
+                PQE e = pq_inf();
+                if (act) {
+                    const int2 nd = __ldg(F.nodes + (size_t)t * F.nnodes + j);
+                    const float qs = __ldg(q + nd.x), v = __int_as_float(nd.y);
+                    e.key = fabs((double)qs - (double)v);
+                    e.tree = t;
+                    e.node = qs < v ? 2 * j + 2 : 2 * j + 1;  // the child not taken
+                    j = qs < v ? 2 * j + 1 : 2 * j + 2;
+                }
+                stage[lane] = e;
+                __syncwarp();
+                const int nb = min(32, F.T - t0);
+                const int keep = min(cap, max(0, budget - F.T));
+                cnt = pq_merge(qa, cnt, stage, nb, qb, keep, sorted);
+                PQE *tmp = qa; qa = qb; qb = tmp;
+                __syncwarp();
+            }
+            if (act && t < budget) out[t] = leaf_code(t, j - nn, F.L);
+        }
+        checked = min(F.T, budget);
+        // ---- pops in queue order
+        while (checked < budget && head < cnt) {
+            const PQE top = qa[head];
+            ++head;
+            // lane 0 descends from the popped node, staging the siblings it passes
+            int nb = 0, leaf = 0;
+            if (lane == 0) {
+                int j = top.node;
+                while (j < nn) {
+                    const int2 nd = __ldg(F.nodes + (size_t)top.tree * F.nnodes + j);
+                    const float qs = __ldg(q + nd.x), v = __int_as_float(nd.y);
+                    PQE e;
+                    e.key = fabs((double)qs - (double)v);
+                    e.tree = top.tree;
+                    e.node = qs < v ? 2 * j + 2 : 2 * j + 1;
+                    j = qs < v ? 2 * j + 1 : 2 * j + 2;
+                    stage[nb++] = e;
+                }
+                leaf = j - nn;
+                out[checked] = leaf_code(top.tree, leaf, F.L);
+            }
+            nb = __shfl_sync(FULL, nb, 0);
+            __syncwarp();
+            ++checked;
+            // drop the popped prefix while merging; keep only what later pops can still take
+            const int keep = min(cap, max(0, budget - checked));
+            cnt = pq_merge(qa + head, cnt - head, stage, nb, qb, keep, sorted);
+            head = 0;
+            PQE *tmp = qa; qa = qb; qb = tmp;
+            __syncwarp();
+        }
+        if (lane == 0) nleaves[qi] = checked;
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+static size_t prio_warp_bytes(int budget) { return (size_t)(2 * (budget + 32) + 64) * sizeof(PQE); }
+
+size_t gf_prio_smem_bytes(int budget) { return prio_warp_bytes(budget); }
+
+int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int budget, unsigned *leaves,
+                          int *nleaves, cudaStream_t st) {
+    const int cap = budget + 32;
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t per_warp = prio_warp_bytes(budget);
+    const int warps = (int)std::min<size_t>(PRIO_WARPS, (size_t)lim / per_warp);
+    if (warps < 1) return gf_fail(GF_EUNSUPPORTED, "leaf budget %d needs %zu B of shared memory", budget, per_warp);
+    const size_t smem = per_warp * warps;
+    if (smem > 48 * 1024) GF_CUDA_TRY(cudaFuncSetAttribute(k_prio_leaves, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long blocks = std::min<long long>((m + warps - 1) / warps, (long long)F->num_sms * 16);
+    k_prio_leaves<<<(unsigned)blocks, warps * 32, smem, st>>>(view_of(F), Q, m, budget, cap, leaves, nleaves);
+    GF_CUDA_TRY(cudaGetLastError());
+    return GF_OK;
+}
+
+extern "C" int gf_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int32_t checks, double eps,
+                              uint32_t *leaves, int32_t *nleaves, int32_t stride, void *stream) {
+    if (!F) return gf_fail(GF_EINVAL, "gf_prio_leaves: null forest");
+    if (m < 0 || checks < 0 || !(eps >= 0.0)) return gf_fail(GF_EINVAL, "gf_prio_leaves: bad arguments");
+    if (m == 0) return GF_OK;
+    if (!Q || !leaves || !nleaves) return gf_fail(GF_EINVAL, "gf_prio_leaves: null pointer");
+    if (((unsigned long long)F->T << F->L) > 0xffffffffull)
+        return gf_fail(GF_EUNSUPPORTED, "priority search needs T * 2^L <= 2^32");
+    const int lb = leaf_budget_of(F, checks, eps);
+    const int budget = lb > 0 ? lb : F->T;
+    if (budget > 4096) return gf_fail(GF_EUNSUPPORTED, "leaf budget %d above 4096", budget);
+    if (stride != budget) return gf_fail(GF_EINVAL, "stride %d, the leaf budget is %d", stride, budget);
+    return gf_launch_prio_leaves(F, Q, m, budget, leaves, nleaves, (cudaStream_t)stream);
+}

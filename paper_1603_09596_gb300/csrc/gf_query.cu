@@ -525,11 +525,12 @@ __global__ void k_query_fused(ForestView F, const float *__restrict__ Q, long lo
 constexpr int LIST = 2048;  // positions per phase
 
 struct StreamLayout {
-    size_t buf, list, qs, pref, lofs, lcnt, lpos, hist, wtmp, sh, total;
+    size_t buf, list, qs, pref, lbase, lcnt, lpos, hist, wtmp, sh, total;
 };
 
 // Every region starts on a 16-byte boundary (the query row is read as float4, the keys as u64).
-__host__ __device__ inline StreamLayout stream_layout(int d, int T, int buf_len) {
+// nl: leaves per query (T for one leaf per tree, the leaf budget for the priority search)
+__host__ __device__ inline StreamLayout stream_layout(int d, int nl, int buf_len) {
     StreamLayout L;
     size_t o = 0;
     auto take = [&o](size_t bytes) {
@@ -541,9 +542,9 @@ __host__ __device__ inline StreamLayout stream_layout(int d, int T, int buf_len)
     L.list = take((size_t)LIST * 4);
     L.qs = take((size_t)ldq_of(d) * 4);
     L.pref = take(16);  // select prefix, threshold
-    L.lofs = take((size_t)T * 4);
-    L.lcnt = take((size_t)T * 4);
-    L.lpos = take((size_t)(T + 1) * 4);
+    L.lbase = take((size_t)nl * 8);
+    L.lcnt = take((size_t)nl * 4);
+    L.lpos = take((size_t)(nl + 1) * 4);
     L.hist = take(256 * 4);
     L.wtmp = take(64 * 4);
     L.sh = take(8 * 4);
@@ -562,9 +563,10 @@ __device__ __forceinline__ int tree_of_pos(const int *lpos, int T, int pos) {
     return lo;
 }
 
-__device__ __forceinline__ int id_at(const ForestView &F, const int *lpos, const int *lofs, int pos) {
-    const int t = tree_of_pos(lpos, F.T, pos);
-    return __ldg(F.perm + (size_t)t * F.n + lofs[t] + (pos - lpos[t]));
+// id at concatenated position pos: leaf j's ids start at perm offset lbase[j]
+__device__ __forceinline__ int id_at(const ForestView &F, const int *lpos, const long long *lbase, int nl, int pos) {
+    const int j = tree_of_pos(lpos, nl, pos);
+    return __ldg(F.perm + lbase[j] + (pos - lpos[j]));
 }
 
 // In-place stable compaction of buf[0..cnt) to the keys <= kth.
@@ -672,21 +674,24 @@ __device__ void rescore_f32(const ForestView &F, const float *qs, const int *ids
 template <int PREC, int NC, int NCF, int G>
 __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const float *__restrict__ Q, long long m,
                                                       int k, int R, int buf_len, unsigned *bitmaps, int nwords,
-                                                      const int *__restrict__ order, long long *ids,
-                                                      float *dists, int *ncand_out) {
+                                                      const int *__restrict__ order,
+                                                      const unsigned *__restrict__ leaf_list,
+                                                      const int *__restrict__ nleaf_list, int nl_max,
+                                                      long long *ids, float *dists, int *ncand_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const StreamLayout Ly = stream_layout(F.d, F.T, buf_len);
+    const StreamLayout Ly = stream_layout(F.d, nl_max, buf_len);
     unsigned long long *buf = reinterpret_cast<unsigned long long *>(smem_raw + Ly.buf);
     int *list = reinterpret_cast<int *>(smem_raw + Ly.list);
     float *qs = reinterpret_cast<float *>(smem_raw + Ly.qs);
     unsigned long long *pref = reinterpret_cast<unsigned long long *>(smem_raw + Ly.pref);
     unsigned long long *thr = pref + 1;
-    int *lofs = reinterpret_cast<int *>(smem_raw + Ly.lofs);
+    long long *lbase = reinterpret_cast<long long *>(smem_raw + Ly.lbase);
     int *lcnt = reinterpret_cast<int *>(smem_raw + Ly.lcnt);
     int *lpos = reinterpret_cast<int *>(smem_raw + Ly.lpos);
     unsigned *hist = reinterpret_cast<unsigned *>(smem_raw + Ly.hist);
     int *wtmp = reinterpret_cast<int *>(smem_raw + Ly.wtmp);
     // sh: [0] compaction scratch [1] buffer count [2] positions [3] admitted ids [4] select [5] list count
+    //     [6] leaves of the current query
     int *sh = reinterpret_cast<int *>(smem_raw + Ly.sh);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int keep = PREC == P_F32 ? k : R;
@@ -697,19 +702,35 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
         const long long qi = order ? (long long)order[qs_i] : qs_i;  // CTAs walk the batch in `order`
         load_query(Q + qi * F.d, F.d, qs);
         __syncthreads();
-        for (int t = threadIdx.x; t < F.T; t += blockDim.x)
-            leaf_range(F, t, descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, qs), lofs, lcnt);
+        // the leaves this query checks: one per tree (descent, Eq. 1) or a given list
+        const int nl = leaf_list ? min(nleaf_list[qi], nl_max) : F.T;
+        for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+            int t, b;
+            if (leaf_list) {
+                const unsigned code = leaf_list[qi * nl_max + j];
+                t = (int)(code >> F.L);
+                b = (int)(code & ((1u << F.L) - 1u));
+            } else {
+                t = j;
+                b = descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, qs);
+            }
+            const long long lo = ((long long)b * F.n) >> F.L;
+            const long long hi = ((long long)(b + 1) * F.n) >> F.L;
+            lbase[j] = (long long)t * F.n + lo;
+            lcnt[j] = (int)(hi - lo);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             int acc = 0;
-            for (int t = 0; t < F.T; ++t) {
-                lpos[t] = acc;
-                acc += lcnt[t];
+            for (int j = 0; j < nl; ++j) {
+                lpos[j] = acc;
+                acc += lcnt[j];
             }
-            lpos[F.T] = acc;
+            lpos[nl] = acc;
             sh[1] = 0;
             sh[2] = acc;
             sh[3] = 0;
+            sh[6] = nl;
             *thr = KEY_NONE;
         }
         __syncthreads();
@@ -725,7 +746,7 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int off = b0 + u * blockDim.x + threadIdx.x;
-                    id[u] = off < pend ? id_at(F, lpos, lofs, p0 + off) : -1;
+                    id[u] = off < pend ? id_at(F, lpos, lbase, nl, p0 + off) : -1;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
@@ -741,19 +762,19 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
                 }
             }
             __syncthreads();
-            const int nl = sh[5];
+            const int nadm = sh[5];
             // ---- B: score the admitted rows, G per warp at a time
-            for (int j0 = w * G; j0 < nl; j0 += nw * G) {
+            for (int j0 = w * G; j0 < nadm; j0 += nw * G) {
                 int rid[G];
                 float dd[G];
 #pragma unroll
-                for (int g = 0; g < G; ++g) rid[g] = list[min(j0 + g, nl - 1)];
+                for (int g = 0; g < G; ++g) rid[g] = list[min(j0 + g, nadm - 1)];
                 warp_dist_g<PREC, NC, G>(F, qs, rid, dd);
                 if (lane == 0) {
                     const unsigned long long th = *reinterpret_cast<volatile unsigned long long *>(thr);
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
-                        if (j0 + g >= nl) break;
+                        if (j0 + g >= nadm) break;
                         const unsigned long long key = make_key(dd[g], rid[g]);
                         if (key < th) buf[atomicAdd(&sh[1], 1)] = key;
                     }
@@ -761,7 +782,7 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
             }
             __syncthreads();
             const int cnt_now = sh[1];
-            if (threadIdx.x == 0) sh[3] += nl;
+            if (threadIdx.x == 0) sh[3] += nadm;
             __syncthreads();  // every thread has read the count before it changes
             if (cnt_now > keep) {
                 const unsigned long long kth = gfdev::block_select(buf, cnt_now, keep - 1, hist, pref, &sh[4]);
@@ -782,7 +803,7 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
             sort_keys(buf, cnt);
         }
         write_topk(buf, cnt, k, ids + qi * k, dists + qi * k);
-        for (int pos = threadIdx.x; pos < tot; pos += blockDim.x) bm[id_at(F, lpos, lofs, pos) >> 5] = 0u;
+        for (int pos = threadIdx.x; pos < tot; pos += blockDim.x) bm[id_at(F, lpos, lbase, nl, pos) >> 5] = 0u;
         if (threadIdx.x == 0 && ncand_out) ncand_out[qi] = sh[3];
         __syncthreads();
     }
@@ -871,6 +892,28 @@ int launch_fused(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32
     return GF_OK;
 }
 
+// Device scratch of one streaming launch, in this order (each part 16-byte aligned):
+//   bitmaps  grid * ceil(n/32) words, zero between queries
+//   okeys    m * 8  and  order  m * 4          (locality order)
+//   leaves   m * nl * 4  and  nleaves  m * 4   (priority search leaf lists)
+struct StreamWorkspace {
+    size_t okeys, order, leaves, nleaves, total;
+};
+
+StreamWorkspace stream_workspace(const gf_forest *F, long long m, long long grid, bool ordered, int nl) {
+    auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    StreamWorkspace W;
+    size_t o = al((size_t)grid * ((F->n + 31) / 32) * 4);
+    W.okeys = o;
+    W.order = ordered ? al(o + (size_t)m * 8) : o;
+    o = ordered ? al(W.order + (size_t)m * 4) : o;
+    W.leaves = o;
+    W.nleaves = nl > 0 ? al(o + (size_t)m * nl * 4) : o;
+    o = nl > 0 ? al(W.nleaves + (size_t)m * 4) : o;
+    W.total = o;
+    return W;
+}
+
 // buffer: the kept keys plus one phase of appends
 int stream_buf_len(int keep) { return keep + LIST; }
 
@@ -885,7 +928,9 @@ int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
     const int keep = PREC == P_F32 ? k : R;
     if (keep > LIST) return gf_fail(GF_EUNSUPPORTED, "k or R = %d above %d", keep, LIST);
     const int buf_len = stream_buf_len(keep);
-    const size_t smem = stream_layout(F->d, F->T, buf_len).total;
+    const bool prio = x.leaf_budget > F->T;  // Alg. 2 priority search: a leaf list per query
+    const int nl_max = prio ? x.leaf_budget : F->T;
+    const size_t smem = stream_layout(F->d, nl_max, buf_len).total;
     int r = check_smem(F, smem);
     if (r) return r;
     if (warps > 8) return gf_fail(GF_EINVAL, "warps_per_cta=%d above 8 for the streaming kernel", warps);
@@ -910,8 +955,8 @@ int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
     }
     const int nwords = (int)((F->n + 31) / 32);
     const bool ordered = x.order == GF_ORDER_LOCALITY || (x.order == GF_ORDER_AUTO && m > grid);
-    const size_t bm_bytes = (size_t)grid * nwords * 4;
-    const size_t ws_bytes = bm_bytes + (ordered ? (size_t)m * 12 + 16 : 0);
+    const StreamWorkspace W = stream_workspace(F, m, grid, ordered, prio ? nl_max : 0);
+    const size_t ws_bytes = W.total;
     unsigned *bitmaps = (unsigned *)x.workspace;
     bool own = false;
     if (bitmaps) {
@@ -928,10 +973,19 @@ int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         if (e != cudaSuccess) { cudaFreeAsync(bitmaps, st); return gf_cuda_fail(e, "workspace memset"); }
     }
     int *order = nullptr;
+    unsigned *leaf_list = nullptr;
+    int *nleaf_list = nullptr;
+    if (prio) {
+        leaf_list = (unsigned *)((char *)bitmaps + W.leaves);
+        nleaf_list = (int *)((char *)bitmaps + W.nleaves);
+        if ((r = gf_launch_prio_leaves(F, Q, m, nl_max, leaf_list, nleaf_list, st))) {
+            if (own) cudaFreeAsync(bitmaps, st);
+            return r;
+        }
+    }
     if (ordered) {
-        // keys (8 B) then order (4 B) per query, after the bitmaps (16-byte aligned)
-        unsigned long long *okeys = (unsigned long long *)((char *)bitmaps + ((bm_bytes + 15) & ~(size_t)15));
-        order = (int *)(okeys + m);
+        unsigned long long *okeys = (unsigned long long *)((char *)bitmaps + W.okeys);
+        order = (int *)((char *)bitmaps + W.order);
         k_order_keys<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(view_of(F), Q, m, okeys);
         const long long chunks = (m + ORDER_CHUNK - 1) / ORDER_CHUNK;
         const int P = next_pow2((int)std::min<long long>(m, ORDER_CHUNK));
@@ -943,7 +997,8 @@ int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         k_order_sort<<<(unsigned)chunks, 1024, osmem, st>>>(m, okeys, order);
     }
     kern<<<(unsigned)grid, threads, smem, st>>>(view_of(F), Q, m, k, R, buf_len, bitmaps, nwords, order,
-                                               (long long *)ids, dists, x.ncand_out);
+                                               leaf_list, nleaf_list, nl_max, (long long *)ids, dists,
+                                               x.ncand_out);
     cudaError_t e = cudaGetLastError();
     if (own) cudaFreeAsync(bitmaps, st);
     if (e != cudaSuccess) return gf_cuda_fail(e, "k_query_stream launch");
@@ -985,6 +1040,10 @@ int dispatch_prec(const gf_forest *F, const float *Q, int64_t m, int32_t k, int3
     const int ncf = nc_for(F->ldx / 4);
     const int nc = nc_for(chunks);
     int algo = x.algo;
+    if (x.leaf_budget > F->T) {
+        if (algo == GF_ALGO_SORT) return gf_fail(GF_EINVAL, "the priority search runs in the streaming kernel only");
+        algo = GF_ALGO_STREAM;
+    }
     if (algo == GF_ALGO_AUTO) {
         const size_t sort_smem = smem_bytes(F->d, F->T, F->cand_cap);
         algo = (F->cand_cap <= 4096 && sort_smem <= 100 * 1024 && !x.ncand_out) ? GF_ALGO_SORT : GF_ALGO_STREAM;
@@ -1017,6 +1076,12 @@ int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         case GF_FP8_RERANK: return dispatch_prec<P_FP8>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x);
     }
     return gf_fail(GF_EINVAL, "unknown precision %d", precision);
+}
+
+int gf_stream_workspace_bytes(const gf_forest *F, int64_t m, long long grid, bool ordered, int leaf_budget,
+                              int64_t *bytes) {
+    *bytes = (int64_t)stream_workspace(F, m, grid, ordered, leaf_budget > F->T ? leaf_budget : 0).total;
+    return GF_OK;
 }
 
 int gf_stream_grid(const gf_forest *F, int64_t m, int warps, int ctas_per_sm, int precision, int k, int R,

@@ -39,7 +39,7 @@ class QueryOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rerank_R", C.c_int32), ("warps_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("stream", C.c_void_p), ("algo", C.c_int32),
                 ("rows_in_flight", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64),
-                ("ncand_out", C.c_void_p), ("order", C.c_int32), ("reserved", C.c_int32)]
+                ("ncand_out", C.c_void_p), ("order", C.c_int32), ("checks", C.c_int32), ("eps", C.c_double)]
 
 
 class ServerOpts(C.Structure):
@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
             "gf_candidates": ([P, P, i64, P, P, P], i32),
             "gf_score_topk": ([P, P, i64, P, P, i32, i32, P, P, P], i32),
             "gf_score_screened": ([P, P, i64, P, P, i32, i32, P, P], i32),
+            "gf_prio_leaves": ([P, P, i64, i32, C.c_double, P, P, i32, P], i32),
             "gf_server_opts_default": ([P], None),
             "gf_server_create": ([P, i32, P, P], i32),
             "gf_server_slots": ([P], i32),
@@ -213,9 +214,9 @@ def gf_forest_set_tuning(F: Forest, precision: int, warps_per_cta: int, ctas_per
 
 
 def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
-          rows_in_flight=0, order=GF_ORDER_AUTO):
+          rows_in_flight=0, order=GF_ORDER_AUTO, checks=0, eps=0.0):
     o = QueryOpts(precision, rerank_R, warps_per_cta, ctas_per_sm, _stream(stream), algo, rows_in_flight,
-                  None, 0, None, order, 0)
+                  None, 0, None, order, checks, eps)
     if workspace is not None:
         o.workspace = _dptr(workspace, workspace.dtype, "workspace")
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -227,7 +228,7 @@ def _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspa
 def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, rerank_R: int = 0,
              warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None, algo: int = GF_ALGO_AUTO,
              workspace: torch.Tensor | None = None, ncand_out: torch.Tensor | None = None,
-             rows_in_flight: int = 0, order: int = GF_ORDER_AUTO,
+             rows_in_flight: int = 0, order: int = GF_ORDER_AUTO, checks: int = 0, eps: float = 0.0,
              out: tuple[torch.Tensor, torch.Tensor] | None = None):
     """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k])."""
     m = Q.shape[0]
@@ -237,15 +238,17 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
     else:
         ids, dists = out
     o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
-              rows_in_flight, order)
+              rows_in_flight, order, checks, eps)
     _check(lib().gf_query_ex(F.handle, _dptr(Q, torch.float32, "Q"), m, k, C.byref(o),
                              _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists")))
     return ids, dists
 
 
 def gf_query_workspace_size(F: Forest, m: int, precision: int = GF_FP32, rerank_R: int = 0,
-                            warps_per_cta: int = 0, ctas_per_sm: int = 0, order: int = GF_ORDER_AUTO) -> int:
-    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, None, GF_ALGO_STREAM, None, None, 0, order)
+                            warps_per_cta: int = 0, ctas_per_sm: int = 0, order: int = GF_ORDER_AUTO,
+                            checks: int = 0, eps: float = 0.0) -> int:
+    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, None, GF_ALGO_STREAM, None, None, 0, order,
+              checks, eps)
     b = C.c_int64()
     _check(lib().gf_query_workspace_size(F.handle, m, C.byref(o), C.byref(b)))
     return b.value
@@ -354,6 +357,29 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def leaf_budget(F: Forest, checks: int, eps: float = 0.0) -> int:
+    """Leaves the priority search checks per query: max(T, ceil(c / (1 + eps)))."""
+    T = F.info.T
+    if checks <= T:
+        return T
+    b = checks / (1.0 + eps)
+    nl = T
+    while nl < b:
+        nl += 1
+    return nl
+
+
+def gf_prio_leaves(F: Forest, Q: torch.Tensor, checks: int, eps: float = 0.0, stream=None):
+    m = Q.shape[0]
+    nb = leaf_budget(F, checks, eps)
+    leaves = torch.zeros((m, nb), dtype=torch.int32, device=Q.device)
+    nl = torch.empty((m,), dtype=torch.int32, device=Q.device)
+    _check(lib().gf_prio_leaves(F.handle, _dptr(Q, torch.float32, "Q"), m, checks, eps,
+                                _dptr(leaves, torch.int32, "leaves"), _dptr(nl, torch.int32, "nleaves"),
+                                nb, _stream(stream)))
+    return leaves, nl
 
 
 def gf_version() -> int:

@@ -339,3 +339,71 @@ def test_locality_order_changes_no_result(gf, prec):
     for order in (gf.GF_ORDER_LOCALITY, gf.GF_ORDER_AUTO):
         b = res[order]
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+
+
+# ---------------------------------------------------------------- Alg. 2 priority search
+
+@pytest.mark.parametrize("name,c", [("tiny", 24), ("ragged", 23), ("manytrees", 100), ("gist_like", 64),
+                                    ("klein", 32)])
+def test_priority_leaf_order_bit_exact(gf, name, c):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    leaves, nl = gf.gf_prio_leaves(G, torch.from_numpy(Q).cuda(), c)
+    leaves = leaves.cpu().numpy().view(np.uint32).astype(np.int64)
+    _, _, _, onl, oseq = oracle.search_priority(F, X, Q, 1, c, return_leaves=True)
+    assert np.array_equal(nl.cpu().numpy(), onl)
+    for i in range(Q.shape[0]):
+        assert np.array_equal(leaves[i, :onl[i]], oseq[i, :onl[i]])
+
+
+@pytest.mark.parametrize("name,c,eps", [("tiny", 24, 0.0), ("ragged", 23, 0.0), ("manytrees", 100, 0.5),
+                                        ("gist_like", 64, 0.0), ("klein", 32, 0.1)])
+@pytest.mark.parametrize("k", [1, 10])
+def test_priority_search_matches_oracle(gf, name, c, eps, k):
+    X, Q, F = case(name)
+    G, _ = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    nc = torch.full((Q.shape[0],), -1, dtype=torch.int32, device="cuda")
+    gi, gd = gf.gf_query(G, Qg, k, checks=c, eps=eps, ncand_out=nc)
+    oi, od, onc, onl = oracle.search_priority(F, X, Q, k, c, eps)
+    assert np.array_equal(nc.cpu().numpy(), onc)   # the same leaves, each id admitted once
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+
+
+def test_priority_with_c_equal_T_is_the_one_leaf_search(gf):
+    X, Q, F = case("gist_like")
+    G, _ = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    a = gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_STREAM)
+    b = gf.gf_query(G, Qg, 10, checks=F.T)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_priority_with_screening(gf, prec):
+    X, Q, F = case("gist_like")
+    G, _ = gpu_forest(gf, X, F)
+    gf.gf_forest_add_screen(G, gf.PRECISIONS[prec])
+    Qg = torch.from_numpy(Q).cuda()
+    full = gf.gf_query(G, Qg, 10, checks=48)
+    # a shortlist of every candidate gives the float32 answer exactly
+    scr = gf.gf_query(G, Qg, 10, checks=48, precision=gf.PRECISIONS[prec], rerank_R=2048)
+    assert torch.equal(full[0], scr[0]) and torch.equal(full[1], scr[1])
+
+
+def test_exact_neighbours_by_one_leaf_forest(gf):
+    # leaf_size >= n: the library's own kernel scans every point, which is exact k-NN
+    from paper_1603_09596_gb300 import autotune
+    X, Q, F = case("ragged")
+    ids, d = autotune.exact_neighbours(torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda(), 3)
+    ei, ed = oracle.bruteforce(X, Q, 3)
+    assert_topk_close(X, Q, ids.cpu().numpy(), d.cpu().numpy(), ei, ed)
+
+
+def test_configure_meets_recall_target(gf):
+    from paper_1603_09596_gb300 import autotune
+    X, Q = synth.manifold(20_000, 100, 200, "klein", seed=5, qseed=6)
+    res = autotune.configure(torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda(), target_recall=0.9,
+                             grid=[(8, 32, 0), (16, 64, 0), (16, 64, 64), (32, 256, 0)])
+    assert res["met_target"] and res["choice"]["recall_at_1"] >= 0.9
+    assert len(res["tried"]) == 4
