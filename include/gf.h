@@ -53,7 +53,7 @@ typedef struct gf_rand_params {
     int32_t shuffle;     /* 1: per-tree random order breaks ties of equal coordinates
                             (Sec. 2.1 "Shuffling"); 0: ties broken by point id */
     int32_t var_scope;   /* GF_VAR_NODE or GF_VAR_GLOBAL */
-    int32_t householder; /* per-tree random reflection (Sec. 2.2); must be 0 (GF_EUNSUPPORTED) */
+    int32_t householder; /* per-tree reflection (Sec. 2.2): only with gf_build_reflected */
 } gf_rand_params;
 
 /* Candidate scoring precision (how the leaf points are ranked, Sec. 3 "Distance computation"). */
@@ -127,7 +127,7 @@ void gf_query_opts_default(gf_query_opts *o);    /* FP32, everything else 0 / NU
  *   rp         NULL for defaults
  *   seed       forest seed: the same (X, parameters, seed) always gives the same forest
  *   out        receives the new forest
- * Errors: GF_EINVAL (bad sizes, NaN/Inf in X, t outside [1, d]), GF_EUNSUPPORTED (householder),
+ * Errors: GF_EINVAL (bad sizes, NaN/Inf in X, t outside [1, d], householder without vectors),
  * GF_ENOMEM, GF_ECUDA.  Synchronous.
  */
 int gf_build(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
@@ -138,6 +138,23 @@ int gf_build(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
 int gf_build_ex(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
                 const gf_rand_params *rp, uint64_t seed, int32_t borrow_x, void *stream,
                 gf_forest **out);
+
+/*
+ * gf_build_reflected -- gf_build_ex with a Householder reflection per tree (Sec. 2.2): tree t is
+ * built on P_t x = x - 2 (u_t^T x) u_t, and every query is reflected the same way before it
+ * descends tree t (Sec. 2.3); distances are always between the original query and points.
+ *   U_host  host [T][d] float32, the vectors u_t (unit length expected; used as given), copied
+ * The reflection is evaluated in float32 in a fixed order, every multiply and add rounded on its
+ * own: w2 = 2 * sum_j u_j x_j over j ascending, then x'_j = x_j - w2 * u_j.  A global variance
+ * scope is not defined for reflected points (GF_EINVAL).  Other arguments and errors as gf_build_ex.
+ */
+int gf_build_reflected(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
+                       const gf_rand_params *rp, uint64_t seed, const float *U_host,
+                       int32_t borrow_x, void *stream, gf_forest **out);
+
+/* Give a forest (e.g. an imported one) per-tree Householder vectors, host [T][d] float32: from
+ * now on its queries are reflected before descending.  Errors: GF_EINVAL (NaN/Inf), GF_ENOMEM. */
+int gf_forest_set_reflections(gf_forest *F, const float *U_host);
 
 /*
  * gf_forest_import -- make a forest from a given tree structure (used to query a forest built
@@ -286,7 +303,8 @@ typedef struct gf_server_opts {
     int32_t k_max;             /* largest k a request may ask for (default 10) */
     int32_t precision;         /* GF_FP32 / GF_BF16_RERANK / GF_FP8_RERANK for every batch */
     int32_t rerank_R;          /* shortlist for the screened precisions (0 = forest default) */
-    int32_t reserved;
+    int32_t checks;            /* leaf checks c of every batch (gf_query_opts.checks) */
+    double eps;                /* gf_query_opts.eps */
 } gf_server_opts;
 
 typedef struct gf_server_stats {

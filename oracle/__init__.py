@@ -58,7 +58,14 @@ def lib():
         L.gfo_search.restype = None
         L.gfo_bruteforce.argtypes = [P, i64, i32, P, i64, i32, P, P]; L.gfo_bruteforce.restype = None
         L.gfo_search_priority.argtypes = [P, i64, i32, P, P, P, i32, i32, P, i64, i32, i64, C.c_double,
-                                          P, P, P, P, P, i64]
+                                          P, P, P, P, P, i64, P]
+        L.gfo_reflect.argtypes = [P, P, i32, P]; L.gfo_reflect.restype = None
+        L.gfo_build_reflected.argtypes = [P, i64, i32, i32, i32, i32, i32, i32, u64, P, P, P, P]
+        L.gfo_build_reflected.restype = i32
+        L.gfo_descend_reflected.argtypes = [P, P, i32, i32, P, i64, i32, P, P]
+        L.gfo_descend_reflected.restype = None
+        L.gfo_search_reflected.argtypes = [P, i64, i32, P, P, P, i32, i32, P, i64, i32, P, P, P, P]
+        L.gfo_search_reflected.restype = None
         L.gfo_search_priority.restype = None
         L.gfo_num_threads.argtypes = []; L.gfo_num_threads.restype = i32
         _lib = L
@@ -131,14 +138,16 @@ class Forest:
     split_dim: np.ndarray  # int32 [T, 2^L - 1]
     split_val: np.ndarray  # float32 [T, 2^L - 1]
     perm: np.ndarray       # int32 [T, n]
+    U: np.ndarray | None = None  # float32 [T, d]: per-tree Householder vectors (Sec. 2.2), or None
 
     def leaf_range(self, b: int) -> tuple[int, int]:
         return (b * self.n) >> self.L, ((b + 1) * self.n) >> self.L
 
 
 def build_forest(X: np.ndarray, T: int, leaf_size: int, t: int = 5, shuffle: int = 1,
-                 var_scope: int = 0, seed: int = 0) -> Forest:
-    """Alg. 1: T randomized trees on X (readings R1-R5 of gf_oracle.c)."""
+                 var_scope: int = 0, seed: int = 0, U: np.ndarray | None = None) -> Forest:
+    """Alg. 1: T randomized trees on X (readings R1-R5 of gf_oracle.c); with U [T, d] each tree is
+    built on its Householder-reflected points (Sec. 2.2)."""
     X = _f32(X)
     n, d = X.shape
     L = depth(n, leaf_size)
@@ -146,11 +155,29 @@ def build_forest(X: np.ndarray, T: int, leaf_size: int, t: int = 5, shuffle: int
     sd = np.zeros((T, nn), dtype=np.int32)
     sv = np.zeros((T, nn), dtype=np.float32)
     pm = np.zeros((T, n), dtype=np.int32)
-    r = lib().gfo_build(_p(X), n, d, T, leaf_size, t, shuffle, var_scope, seed, _p(sd), _p(sv), _p(pm))
+    Up = None
+    if U is not None:
+        U = _f32(U)
+        assert U.shape == (T, d)
+        Up = _p(U)
+    r = lib().gfo_build_reflected(_p(X), n, d, T, leaf_size, t, shuffle, var_scope, seed, Up, _p(sd), _p(sv),
+                                  _p(pm))
     if r < 0:
         raise ValueError("gfo_build: invalid arguments")
     assert r == L
-    return Forest(n, d, T, leaf_size, L, sd, sv, pm)
+    return Forest(n, d, T, leaf_size, L, sd, sv, pm, U)
+
+
+def reflect(x: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Px = x - 2 (u^T x) u (Sec. 2.2), with the rounding steps gfo_reflect fixes."""
+    x, u = _f32(x), _f32(u)
+    out = np.empty_like(x)
+    lib().gfo_reflect(_p(x), _p(u), x.shape[0], _p(out))
+    return out
+
+
+def _Up(F: "Forest"):
+    return _p(np.ascontiguousarray(F.U, dtype=np.float32)) if F.U is not None else None
 
 
 # ---------------------------------------------------------------- search
@@ -160,8 +187,8 @@ def descend(F: Forest, Q: np.ndarray) -> np.ndarray:
     Q = _f32(Q)
     m = Q.shape[0]
     leaf = np.empty((m, F.T), dtype=np.int32)
-    lib().gfo_descend(_p(np.ascontiguousarray(F.split_dim)), _p(np.ascontiguousarray(F.split_val)),
-                      F.L, F.T, _p(Q), m, F.d, _p(leaf))
+    lib().gfo_descend_reflected(_p(np.ascontiguousarray(F.split_dim)), _p(np.ascontiguousarray(F.split_val)),
+                                F.L, F.T, _p(Q), m, F.d, _Up(F), _p(leaf))
     return leaf
 
 
@@ -196,9 +223,9 @@ def search(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, return_ncand: bool =
     oi = np.empty((m, k), dtype=np.int64)
     od = np.empty((m, k), dtype=np.float64)
     nc = np.empty(m, dtype=np.int64)
-    lib().gfo_search(_p(X), F.n, F.d, _p(np.ascontiguousarray(F.split_dim)),
-                     _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
-                     F.L, F.T, _p(Q), m, k, _p(oi), _p(od), _p(nc))
+    lib().gfo_search_reflected(_p(X), F.n, F.d, _p(np.ascontiguousarray(F.split_dim)),
+                               _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
+                               F.L, F.T, _p(Q), m, k, _Up(F), _p(oi), _p(od), _p(nc))
     return (oi, od, nc) if return_ncand else (oi, od)
 
 
@@ -217,7 +244,8 @@ def search_priority(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, c: int, eps
     seq = np.full((m, cap), -1, dtype=np.int64)
     lib().gfo_search_priority(_p(X), F.n, F.d, _p(np.ascontiguousarray(F.split_dim)),
                               _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
-                              F.L, F.T, _p(Q), m, k, c, eps, _p(oi), _p(od), _p(nc), _p(nl), _p(seq), cap)
+                              F.L, F.T, _p(Q), m, k, c, eps, _p(oi), _p(od), _p(nc), _p(nl), _p(seq), cap,
+                              _Up(F))
     return (oi, od, nc, nl, seq) if return_leaves else (oi, od, nc, nl)
 
 

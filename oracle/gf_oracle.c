@@ -100,6 +100,22 @@ static int64_t pos_of(int64_t n, int32_t l, int64_t a) {
     return (int64_t)(((__int128)a * n) >> l);
 }
 
+/* ------------------------------------------------------------------ Householder reflection */
+
+/*
+ * Sec. 2.2: the reflection of x across the hyperplane normal to u is Px = x - 2 (u^T x) u.  Here
+ * u is taken as given (a unit vector is expected).  Reading: the reflection only shapes the trees,
+ * so it is evaluated in float32 with a fixed order -- w = u^T x summed over j ascending, then each
+ * coordinate x_j - (2w) u_j -- every multiply and add rounded on its own (this file is compiled
+ * without fused multiply-add).
+ */
+void gfo_reflect(const float *x, const float *u, int32_t d, float *out) {
+    float w = 0.0f;
+    for (int32_t j = 0; j < d; j++) w = w + u[j] * x[j];
+    const float w2 = 2.0f * w;
+    for (int32_t j = 0; j < d; j++) out[j] = x[j] - w2 * u[j];
+}
+
 /* ------------------------------------------------------------------ Alg. 3 variance */
 
 /*
@@ -240,13 +256,26 @@ static void build_node(build_ctx *c, int32_t l, int64_t a) {
  * Trees are independent and built one per thread (Sec. 3 "Parallelization").
  * Returns L, or -1 on invalid arguments.
  */
+int32_t gfo_build_reflected(const float *X, int64_t n, int32_t d, int32_t T, int32_t p, int32_t t,
+                            int32_t shuffle, int32_t var_scope, uint64_t seed, const float *U,
+                            int32_t *split_dim, float *split_val, int32_t *perm);
+
 int32_t gfo_build(const float *X, int64_t n, int32_t d, int32_t T, int32_t p, int32_t t,
                   int32_t shuffle, int32_t var_scope, uint64_t seed, int32_t *split_dim,
                   float *split_val, int32_t *perm) {
+    return gfo_build_reflected(X, n, d, T, p, t, shuffle, var_scope, seed, NULL, split_dim, split_val, perm);
+}
+
+/* As gfo_build; with U (T x d) every tree is built on its own reflected points P_t X (Sec. 2.2:
+ * "build on transformed X, store f"). */
+int32_t gfo_build_reflected(const float *X, int64_t n, int32_t d, int32_t T, int32_t p, int32_t t,
+                            int32_t shuffle, int32_t var_scope, uint64_t seed, const float *U,
+                            int32_t *split_dim, float *split_val, int32_t *perm) {
     if (!X || n < 1 || d < 1 || T < 1 || p < 1 || t < 1 || t > d || n > 0x7FFFFFFFLL) return -1;
     int32_t L = gfo_depth(n, p);
     int64_t nn = ((int64_t)1 << L) - 1;
     int32_t *Dglob = (int32_t *)malloc(sizeof(int32_t) * (size_t)t);
+    if (var_scope == 1 && U) return -1; /* a global ranking of reflected coordinates is per tree */
     if (var_scope == 1) { /* Alg. 1 literal: V and D computed once for the input set */
         int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
         double *var = (double *)malloc(sizeof(double) * (size_t)d);
@@ -259,7 +288,12 @@ int32_t gfo_build(const float *X, int64_t n, int32_t d, int32_t T, int32_t p, in
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t tr = 0; tr < T; tr++) {
         build_ctx c;
-        c.X = X; c.n = n; c.d = d; c.L = L; c.t = t; c.shuffle = shuffle; c.var_scope = var_scope;
+        float *Xt = NULL;
+        if (U) { /* this tree's reflected points */
+            Xt = (float *)malloc(sizeof(float) * (size_t)n * (size_t)d);
+            for (int64_t i = 0; i < n; i++) gfo_reflect(X + i * d, U + (int64_t)tr * d, d, Xt + i * d);
+        }
+        c.X = U ? Xt : X; c.n = n; c.d = d; c.L = L; c.t = t; c.shuffle = shuffle; c.var_scope = var_scope;
         c.tree = tr; c.seed = seed; c.Dglob = Dglob;
         c.split_dim = split_dim + (int64_t)tr * nn;
         c.split_val = split_val + (int64_t)tr * nn;
@@ -270,6 +304,7 @@ int32_t gfo_build(const float *X, int64_t n, int32_t d, int32_t T, int32_t p, in
         build_node(&c, 0, 0);
         free(c.var);
         free(c.D);
+        free(Xt);
     }
     free(Dglob);
     return L;
@@ -289,14 +324,33 @@ int64_t gfo_descend_one(const int32_t *split_dim, const float *split_val, int32_
     return j - (((int64_t)1 << L) - 1);
 }
 
+/* The query a tree's descent sees: q itself, or its reflection P_t q when the forest has U (the
+ * query is reflected before descending, Sec. 2.3; distances still use q). */
+static const float *tree_query(const float *q, const float *U, int32_t t, int32_t d, float *buf) {
+    if (!U) return q;
+    gfo_reflect(q, U + (int64_t)t * d, d, buf);
+    return buf;
+}
+
 /* leaf[i][t] for every query i and tree t. */
+void gfo_descend_reflected(const int32_t *split_dim, const float *split_val, int32_t L, int32_t T,
+                           const float *Q, int64_t m, int32_t d, const float *U, int32_t *leaf) {
+    int64_t nn = ((int64_t)1 << L) - 1;
+#pragma omp parallel
+    {
+        float *buf = (float *)malloc(sizeof(float) * (size_t)d);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < m; i++)
+            for (int32_t t = 0; t < T; t++)
+                leaf[i * T + t] = (int32_t)gfo_descend_one(split_dim + t * nn, split_val + t * nn, L,
+                                                           tree_query(Q + i * d, U, t, d, buf));
+        free(buf);
+    }
+}
+
 void gfo_descend(const int32_t *split_dim, const float *split_val, int32_t L, int32_t T,
                  const float *Q, int64_t m, int32_t d, int32_t *leaf) {
-    int64_t nn = ((int64_t)1 << L) - 1;
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < m; i++)
-        for (int32_t t = 0; t < T; t++)
-            leaf[i * T + t] = (int32_t)gfo_descend_one(split_dim + t * nn, split_val + t * nn, L, Q + i * d);
+    gfo_descend_reflected(split_dim, split_val, L, T, Q, m, d, NULL, leaf);
 }
 
 /* ------------------------------------------------------------------ candidates (R7) */
@@ -394,9 +448,21 @@ void gfo_topk(const float *X, int32_t d, const float *Q, int64_t m, const int64_
  * de-duplicate the leaf points, score them, keep the k nearest.  Queries run in parallel.
  * If ncand is not NULL it receives each query's candidate count.
  */
+void gfo_search_reflected(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
+                          const float *split_val, const int32_t *perm, int32_t L, int32_t T,
+                          const float *Q, int64_t m, int32_t k, const float *U, int64_t *out_ids,
+                          double *out_d, int64_t *ncand);
+
 void gfo_search(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
                 const float *split_val, const int32_t *perm, int32_t L, int32_t T, const float *Q,
                 int64_t m, int32_t k, int64_t *out_ids, double *out_d, int64_t *ncand) {
+    gfo_search_reflected(X, n, d, split_dim, split_val, perm, L, T, Q, m, k, NULL, out_ids, out_d, ncand);
+}
+
+void gfo_search_reflected(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
+                          const float *split_val, const int32_t *perm, int32_t L, int32_t T,
+                          const float *Q, int64_t m, int32_t k, const float *U, int64_t *out_ids,
+                          double *out_d, int64_t *ncand) {
     int64_t nn = ((int64_t)1 << L) - 1;
     int64_t cap = ((n + ((int64_t)1 << L) - 1) >> L) * T;
 #pragma omp parallel
@@ -404,11 +470,13 @@ void gfo_search(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
         int32_t *leaf = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
         int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
         res_t *r = (res_t *)malloc(sizeof(res_t) * (size_t)cap);
+        float *qbuf = (float *)malloc(sizeof(float) * (size_t)d);
 #pragma omp for schedule(dynamic, 4)
         for (int64_t i = 0; i < m; i++) {
             const float *q = Q + i * d;
             for (int32_t t = 0; t < T; t++)
-                leaf[t] = (int32_t)gfo_descend_one(split_dim + t * nn, split_val + t * nn, L, q);
+                leaf[t] = (int32_t)gfo_descend_one(split_dim + t * nn, split_val + t * nn, L,
+                                                   tree_query(q, U, t, d, qbuf));
             int64_t c = gfo_candidates_one(perm, n, L, T, leaf, cand);
             for (int64_t j = 0; j < c; j++) {
                 r[j].id = cand[j];
@@ -420,6 +488,7 @@ void gfo_search(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
         free(leaf);
         free(cand);
         free(r);
+        free(qbuf);
     }
 }
 
@@ -488,7 +557,7 @@ void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *sp
                          const float *split_val, const int32_t *perm, int32_t L, int32_t T,
                          const float *Q, int64_t m, int32_t k, int64_t c, double eps,
                          int64_t *out_ids, double *out_d, int64_t *ncand, int64_t *nleaves,
-                         int64_t *leaf_seq, int64_t seq_cap) {
+                         int64_t *leaf_seq, int64_t seq_cap, const float *U) {
     int64_t nn = ((int64_t)1 << L) - 1;
     double budget = (double)c / (1.0 + eps);
 #pragma omp parallel
@@ -499,9 +568,12 @@ void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *sp
         res_t *best = (res_t *)malloc(sizeof(res_t) * (size_t)k);
         int32_t *touched = NULL;
         int64_t tcap = 0;
+        float *qt = U ? (float *)malloc(sizeof(float) * (size_t)T * (size_t)d) : NULL;
 #pragma omp for schedule(dynamic, 4)
         for (int64_t i = 0; i < m; i++) {
             const float *q = Q + i * d;
+            if (U) /* every tree's reflection of the query, for its descents (Sec. 2.3) */
+                for (int32_t t = 0; t < T; t++) gfo_reflect(q, U + (int64_t)t * d, d, qt + (int64_t)t * d);
             int64_t hs = 0, checked = 0, nc = 0, ntouch = 0;
             kbest_t H = {best, 0, k};
             /* one descent from node j of tree t to a leaf, pushing the siblings, checking the leaf */
@@ -511,12 +583,13 @@ void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *sp
                 int64_t j = (j_);                                                                  \
                 const int32_t *sd = split_dim + (int64_t)tree_ * nn;                               \
                 const float *sv = split_val + (int64_t)tree_ * nn;                                 \
+                const float *qd = U ? qt + (int64_t)tree_ * d : q;                                 \
                 while (j < nn) {                                                                   \
-                    double dd = (double)q[sd[j]] - (double)sv[j];                                  \
+                    double dd = (double)qd[sd[j]] - (double)sv[j];                                 \
                     qent_t pushed_;                                                                \
                     pushed_.key = fabs(dd);                                                        \
                     pushed_.tree = tree_;                                                          \
-                    if (q[sd[j]] < sv[j]) { pushed_.node = 2 * j + 2; j = 2 * j + 1; }             \
+                    if (qd[sd[j]] < sv[j]) { pushed_.node = 2 * j + 2; j = 2 * j + 1; }            \
                     else { pushed_.node = 2 * j + 1; j = 2 * j + 2; }                              \
                     heap_push(heap, &hs, pushed_);                                                 \
                 }                                                                                  \
@@ -558,6 +631,7 @@ void gfo_search_priority(const float *X, int64_t n, int32_t d, const int32_t *sp
         free(heap);
         free(best);
         free(touched);
+        free(qt);
     }
 }
 

@@ -37,9 +37,9 @@ def _time(fn, reps: int = 3) -> float:
 
 
 def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0.995,
-         shapes=SHAPES, r_choices=R_CHOICES) -> dict:
+         shapes=SHAPES, r_choices=R_CHOICES, checks: int = 0) -> dict:
     inf = F.info
-    key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0])
+    key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0], checks)
     if key in _cache:
         res = _cache[key]
         gf.gf_forest_set_tuning(F, precision, res["warps"], res["ctas_per_sm"], res.get("R", 0),
@@ -48,12 +48,12 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
     res: dict = {"precision": precision}
     R = 0
     if precision != gf.GF_FP32:
-        ref_ids, _ = gf.gf_query(F, Q, k)
+        ref_ids, _ = gf.gf_query(F, Q, k, checks=checks)
         R = r_choices[-1]
         for r in r_choices:
             if r < k:
                 continue
-            ids, _ = gf.gf_query(F, Q, k, precision=precision, rerank_R=r)
+            ids, _ = gf.gf_query(F, Q, k, precision=precision, rerank_R=r, checks=checks)
             hit = (ids[:, :, None] == ref_ids[:, None, :]).any(-1).float().mean().item()
             res.setdefault("agreement", {})[r] = hit
             if hit >= agree:
@@ -64,7 +64,7 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
     for w, c, g in shapes:
         try:
             t = _time(lambda: gf.gf_query(F, Q, k, precision=precision, rerank_R=R, warps_per_cta=w,
-                                          ctas_per_sm=c, rows_in_flight=g))
+                                          ctas_per_sm=c, rows_in_flight=g, checks=checks))
         except gf.GFError:
             continue
         timings[(w, c, g)] = t

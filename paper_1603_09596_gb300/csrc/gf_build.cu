@@ -66,7 +66,16 @@ struct BuildParams {
     int2 *nodes;  // [T][2^L - 1]
     int nnodes;
     int *D;       // [TMAX] global top dims (global scope)
+    const float *U;   // [T][d] Householder vectors, or null (trees on X itself)
+    const float *W2;  // [T][n] 2 * u_t^T x_i of every point, when U is set
 };
+
+// Coordinate `dim` of point `id` as tree `tree` sees it: x itself, or its reflection (Sec. 2.2).
+__device__ __forceinline__ float tree_coord(const BuildParams &P, int tree, int id, int dim) {
+    const float x = __ldg(P.x + (size_t)id * P.ldx + dim);
+    if (!P.U) return x;
+    return reflect_coord(x, __ldg(P.W2 + (size_t)tree * P.n + id), __ldg(P.U + (size_t)tree * P.d + dim));
+}
 
 __device__ __forceinline__ unsigned long long tree_key(const BuildParams &P, int tree) {
     return sm64_at(P.seed, (unsigned long long)tree);
@@ -86,10 +95,9 @@ __device__ __forceinline__ float from_ordered(unsigned o) {
     return __uint_as_float((o & 0x80000000u) ? (o ^ 0x80000000u) : ~o);
 }
 
-__device__ __forceinline__ unsigned long long point_key(const BuildParams &P, unsigned long long tk,
+__device__ __forceinline__ unsigned long long point_key(const BuildParams &P, unsigned long long tk, int tree,
                                                         int id, int s) {
-    return ((unsigned long long)ordered_bits(__ldg(P.x + (size_t)id * P.ldx + s)) << 32) |
-           rank_of(P, tk, (unsigned)id);
+    return ((unsigned long long)ordered_bits(tree_coord(P, tree, id, s)) << 32) | rank_of(P, tk, (unsigned)id);
 }
 
 // node geometry at level l
@@ -138,15 +146,17 @@ __device__ __forceinline__ void ff_add(FF &a, float x, float xlo) {
 // below 2^-48 relative and dropped), and both sums are compensated, so the relative error is of
 // order cnt * 2^-48 -- float64 accuracy at float32 instruction rates (GB300's float64 rate is a
 // small fraction of its float32 rate).
-__device__ __forceinline__ void var_accum(const BuildParams &P, const int *__restrict__ rows, long long cnt,
-                                          int krow, int dbase, double S1[DPT], double S2[DPT]) {
-    float K[DPT];
+__device__ __forceinline__ void var_accum(const BuildParams &P, int tree, const int *__restrict__ rows,
+                                          long long cnt, int krow, int dbase, double S1[DPT], double S2[DPT]) {
+    float K[DPT], uu[DPT];
     int dim[DPT];
     FF s1[DPT], s2[DPT];
+    const float *W2 = P.U ? P.W2 + (size_t)tree * P.n : nullptr;
 #pragma unroll
     for (int u = 0; u < DPT; ++u) {
         dim[u] = dbase + threadIdx.x + NT * u;
-        K[u] = dim[u] < P.d ? __ldg(P.x + (size_t)krow * P.ldx + dim[u]) : 0.f;
+        K[u] = dim[u] < P.d ? tree_coord(P, tree, krow, dim[u]) : 0.f;
+        uu[u] = (P.U && dim[u] < P.d) ? __ldg(P.U + (size_t)tree * P.d + dim[u]) : 0.f;
         s1[u] = FF{0.f, 0.f};
         s2[u] = FF{0.f, 0.f};
     }
@@ -161,22 +171,29 @@ __device__ __forceinline__ void var_accum(const BuildParams &P, const int *__res
     };
     long long r = 0;
     for (; r + 4 <= cnt; r += 4) {
-        float v[4][DPT];
+        float v[4][DPT], w2[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float *row = P.x + (size_t)__ldg(rows + r + q) * P.ldx;
+            const int id = __ldg(rows + r + q);
+            const float *row = P.x + (size_t)id * P.ldx;
+            w2[q] = W2 ? __ldg(W2 + id) : 0.f;
 #pragma unroll
             for (int u = 0; u < DPT; ++u) v[q][u] = dim[u] < P.d ? __ldg(row + dim[u]) : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int u = 0; u < DPT; ++u) add(u, v[q][u]);
+            for (int u = 0; u < DPT; ++u) add(u, W2 ? reflect_coord(v[q][u], w2[q], uu[u]) : v[q][u]);
     }
     for (; r < cnt; ++r) {
-        const float *row = P.x + (size_t)__ldg(rows + r) * P.ldx;
+        const int id = __ldg(rows + r);
+        const float *row = P.x + (size_t)id * P.ldx;
+        const float w2 = W2 ? __ldg(W2 + id) : 0.f;
 #pragma unroll
-        for (int u = 0; u < DPT; ++u) add(u, dim[u] < P.d ? __ldg(row + dim[u]) : 0.f);
+        for (int u = 0; u < DPT; ++u) {
+            const float x = dim[u] < P.d ? __ldg(row + dim[u]) : 0.f;
+            add(u, W2 ? reflect_coord(x, w2, uu[u]) : x);
+        }
     }
 #pragma unroll
     for (int u = 0; u < DPT; ++u) {
@@ -307,7 +324,7 @@ __global__ void __launch_bounds__(NT) k_level_small(BuildParams P, int l, const 
         if (threadIdx.x == 0) S.have = 0;
         for (int dbase = 0; dbase < P.d; dbase += DB) {
             double S1[DPT], S2[DPT];
-            var_accum(P, rows, cnt, rows[0], dbase, S1, S2);
+            var_accum(P, g.tree, rows, cnt, rows[0], dbase, S1, S2);
 #pragma unroll
             for (int u = 0; u < DPT; ++u) S.vblk[threadIdx.x + NT * u] = var_of(S1[u], S2[u], cnt);
             topt_merge(S.vblk, min(DB, P.d - dbase), dbase, S.topv, S.topi, &S.have, P.t);
@@ -321,7 +338,7 @@ __global__ void __launch_bounds__(NT) k_level_small(BuildParams P, int l, const 
     __syncthreads();
     const int s = S.s;
     // 3: keys, split key, split value
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) keys[i] = point_key(P, tk, rows[i], s);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) keys[i] = point_key(P, tk, g.tree, rows[i], s);
     __syncthreads();
     unsigned long long kh = ~0ull;
     float v = __int_as_float(0x7f800000);
@@ -360,7 +377,7 @@ __global__ void __launch_bounds__(NT) k_var_partial(BuildParams P, int l, int nc
     const int *seq = pin + (size_t)q.g.tree * P.n;
     const int dbase = blockIdx.y * DB;
     double S1[DPT], S2[DPT];
-    var_accum(P, seq + q.beg, q.end - q.beg, seq[q.g.lo], dbase, S1, S2);
+    var_accum(P, q.g.tree, seq + q.beg, q.end - q.beg, seq[q.g.lo], dbase, S1, S2);
     double *o = part + (size_t)blockIdx.x * 2 * P.d;
 #pragma unroll
     for (int u = 0; u < DPT; ++u) {
@@ -420,7 +437,7 @@ __global__ void k_keys(BuildParams P, int l, const int *__restrict__ pin, const 
         const long long p = gidx - (long long)tree * P.n;
         const long long a = ((((p + 1) << l)) - 1) / P.n;  // node owning position p
         const long long seg = ((long long)tree << l) + a;
-        keys[gidx] = point_key(P, tree_key(P, tree), pin[gidx], seg_s[seg]);
+        keys[gidx] = point_key(P, tree_key(P, tree), tree, pin[gidx], seg_s[seg]);
     }
 }
 
@@ -591,6 +608,22 @@ __global__ void __launch_bounds__(NT) k_part_write(BuildParams P, int l, int nch
     }
 }
 
+// W2[t][i] = 2 * u_t^T x_i, one warp per point and one lane per tree, summed over j ascending with
+// every multiply and add rounded on its own (the order reflect_w2 uses for queries).
+__global__ void k_reflect_w2(const float *__restrict__ x, int ldx, long long n, int d, int T,
+                             const float *__restrict__ U, float *W2) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < n; i += nw) {
+        const float *row = x + i * ldx;
+        for (int t0 = 0; t0 < T; t0 += 32) {
+            const int t = t0 + lane;
+            if (t < T) W2[(size_t)t * n + i] = reflect_w2(U + (size_t)t * d, row, d);
+        }
+    }
+}
+
 __global__ void k_iota(int *perm, long long n, int T) {
     const long long tot = n * T;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < tot;
@@ -627,6 +660,15 @@ static int build_levels(gf_forest *F, const gf_rand_params &rp, uint64_t seed, c
     P.x = F->x; P.n = n; P.d = F->d; P.ldx = F->ldx; P.T = T; P.t = rp.t; P.shuffle = rp.shuffle ? 1 : 0;
     P.global_scope = rp.var_scope == GF_VAR_GLOBAL; P.seed = seed; P.nodes = F->nodes;
     P.nnodes = (1 << L) - 1; P.D = (int *)Dbuf.p;
+    P.U = F->U;
+    P.W2 = nullptr;
+    DevBuf w2buf;
+    if (F->U) {  // every tree sees its reflected points (Sec. 2.2)
+        if ((r = gf_dmalloc(&w2buf.p, (size_t)T * n * 4))) return r;
+        k_reflect_w2<<<F->num_sms * 16, 256, 0, st>>>(F->x, F->ldx, n, F->d, T, F->U, (float *)w2buf.p);
+        GF_CUDA_TRY(cudaGetLastError());
+        P.W2 = (const float *)w2buf.p;
+    }
 
     // chunked-level scratch, sized for the deepest chunked level
     int lc = -1;  // last chunked level
@@ -698,15 +740,35 @@ static int build_levels(gf_forest *F, const gf_rand_params &rp, uint64_t seed, c
     return GF_OK;
 }
 
+int gf_forest_set_U(gf_forest *F, const float *U_host);
+
+static int build_any(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size, const gf_rand_params *rp_in,
+                     uint64_t seed, const float *U_host, int32_t borrow_x, void *stream, gf_forest **out);
+
 extern "C" int gf_build_ex(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
                            const gf_rand_params *rp_in, uint64_t seed, int32_t borrow_x, void *stream,
                            gf_forest **out) {
+    return build_any(X, n, d, T, leaf_size, rp_in, seed, nullptr, borrow_x, stream, out);
+}
+
+extern "C" int gf_build_reflected(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
+                                  const gf_rand_params *rp, uint64_t seed, const float *U_host,
+                                  int32_t borrow_x, void *stream, gf_forest **out) {
+    if (!U_host) return gf_fail(GF_EINVAL, "gf_build_reflected: U is null");
+    return build_any(X, n, d, T, leaf_size, rp, seed, U_host, borrow_x, stream, out);
+}
+
+static int build_any(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size, const gf_rand_params *rp_in,
+                     uint64_t seed, const float *U_host, int32_t borrow_x, void *stream, gf_forest **out) {
     if (!out) return gf_fail(GF_EINVAL, "out is null");
     *out = nullptr;
     gf_rand_params rp;
     gf_rand_params_default(&rp);
     if (rp_in) rp = *rp_in;
-    if (rp.householder) return gf_fail(GF_EUNSUPPORTED, "householder reflections are not implemented");
+    if (rp.householder && !U_host)
+        return gf_fail(GF_EINVAL, "householder = 1 needs the per-tree vectors: use gf_build_reflected");
+    if (U_host && rp.var_scope == GF_VAR_GLOBAL)
+        return gf_fail(GF_EINVAL, "a global variance ranking is not defined for per-tree reflected points");
     if (rp.t < 1 || rp.t > d || rp.t > TMAX) return gf_fail(GF_EINVAL, "t=%d outside [1, min(d, %d)]", rp.t, TMAX);
     if (rp.var_scope != GF_VAR_NODE && rp.var_scope != GF_VAR_GLOBAL) return gf_fail(GF_EINVAL, "bad var_scope");
     if (n >= 1 && leaf_size >= 1) {
@@ -719,6 +781,7 @@ extern "C" int gf_build_ex(const float *X, int64_t n, int32_t d, int32_t T, int3
     int r = gf_forest_alloc(&F, X, n, d, T, leaf_size, borrow_x != 0, st);
     if (r) return r;
     if ((r = gf_check_finite(F->x, (int64_t)n * F->ldx, st))) { gf_forest_destroy(F); return r; }
+    if (U_host && (r = gf_forest_set_U(F, U_host))) { gf_forest_destroy(F); return r; }
     if ((r = build_levels(F, rp, seed, st))) { gf_forest_destroy(F); return r; }
     *out = F;
     return GF_OK;

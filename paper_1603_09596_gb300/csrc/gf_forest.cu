@@ -69,6 +69,7 @@ static void forest_release(gf_forest *F) {
     cudaFree(F->xb);
     cudaFree(F->x8);
     cudaFree(F->scale8);
+    cudaFree(F->U);
     delete F;
 }
 
@@ -219,6 +220,25 @@ extern "C" int gf_forest_get_info(const gf_forest *F, gf_forest_info *info) {
     info->screens = (F->xb ? (1 << GF_BF16_RERANK) : 0) | (F->x8 ? (1 << GF_FP8_RERANK) : 0);
     info->device_bytes = F->device_bytes;
     return GF_OK;
+}
+
+// Copy the per-tree Householder vectors (host [T][d]) into the forest.
+int gf_forest_set_U(gf_forest *F, const float *U_host) {
+    const size_t bytes = (size_t)F->T * F->d * 4;
+    if (!F->U) {
+        int r = gf_dmalloc((void **)&F->U, bytes);
+        if (r) return r;
+        F->device_bytes += (int64_t)bytes;
+    }
+    GF_CUDA_TRY(cudaMemcpy(F->U, U_host, bytes, cudaMemcpyHostToDevice));
+    return GF_OK;
+}
+
+extern "C" int gf_forest_set_reflections(gf_forest *F, const float *U_host) {
+    if (!F || !U_host) return gf_fail(GF_EINVAL, "null argument");
+    for (size_t i = 0; i < (size_t)F->T * F->d; ++i)
+        if (!std::isfinite(U_host[i])) return gf_fail(GF_EINVAL, "U holds NaN/Inf");
+    return gf_forest_set_U(F, U_host);
 }
 
 extern "C" int gf_forest_free(gf_forest *F) {

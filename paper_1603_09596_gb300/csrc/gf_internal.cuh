@@ -31,6 +31,7 @@ struct gf_forest {
     __nv_bfloat16 *xb = nullptr;
     uint8_t *x8 = nullptr;
     float *scale8 = nullptr;
+    float *U = nullptr;  // [T][d] Householder vectors (Sec. 2.2), or null: trees on X itself
     int device = 0;
     int num_sms = 0;
     // per-precision kernel shape and shortlist (written by the autotuner)
@@ -47,6 +48,7 @@ struct ForestView {
     const __nv_bfloat16 *xb;
     const uint8_t *x8;
     const float *scale8;
+    const float *U;  // [T][d] or null
     const int2 *nodes;
     const int32_t *perm;
     long long n;
@@ -55,13 +57,26 @@ struct ForestView {
 
 inline ForestView view_of(const gf_forest *F) {
     ForestView v;
-    v.x = F->x; v.xb = F->xb; v.x8 = F->x8; v.scale8 = F->scale8;
+    v.x = F->x; v.xb = F->xb; v.x8 = F->x8; v.scale8 = F->scale8; v.U = F->U;
     v.nodes = F->nodes; v.perm = F->perm;
     v.n = F->n; v.d = F->d; v.ldx = F->ldx; v.ldb = F->ldb; v.ld8 = F->ld8;
     v.T = F->T; v.L = F->L; v.nnodes = (1 << F->L) - 1;
     v.max_leaf = F->max_leaf; v.cand_cap = F->cand_cap;
     return v;
 }
+
+// ---------------------------------------------------------------- Householder reflection
+// Sec. 2.2: each tree may be built on P x = x - 2 (u^T x) u, and queries are reflected the same way
+// before descending it.  Evaluated in float32 in a fixed order with every multiply and add rounded
+// on its own (no fused multiply-add), so the library and any reference that follows the same order
+// produce identical coordinates: w2 = 2 * sum_j u_j x_j (j ascending), x'_j = x_j - w2 * u_j.
+__device__ __forceinline__ float reflect_w2(const float *u, const float *x, int d) {
+    float w = 0.f;
+    for (int j = 0; j < d; ++j) w = __fadd_rn(w, __fmul_rn(__ldg(u + j), x[j]));
+    return 2.f * w;
+}
+
+__device__ __forceinline__ float reflect_coord(float x, float w2, float u) { return __fsub_rn(x, __fmul_rn(w2, u)); }
 
 // ---------------------------------------------------------------- shape helpers
 
@@ -106,7 +121,7 @@ struct QueryExtra {
 
 int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int budget, unsigned *leaves,
                           int *nleaves, cudaStream_t st);
-size_t gf_prio_smem_bytes(int budget);
+size_t gf_prio_smem_bytes(int budget, int T);
 int gf_stream_workspace_bytes(const gf_forest *F, int64_t m, long long grid, bool ordered, int leaf_budget,
                               int64_t *bytes);
 

@@ -85,14 +85,21 @@ __device__ __forceinline__ unsigned leaf_code(int tree, int leaf, int L) {
     return ((unsigned)tree << L) | (unsigned)leaf;
 }
 
+// per-warp shared memory: two queue arrays of `cap` entries, the staged batch and its sorted copy,
+// then one reflection weight per tree
+__host__ __device__ inline size_t prio_warp_bytes(int budget, int T) {
+    return (size_t)(2 * (budget + 32) + 64) * sizeof(PQE) + (size_t)(T + 3) / 4 * 16;
+}
+
 __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, const float *__restrict__ Q,
                                                                 long long m, int budget, int cap,
                                                                 unsigned *leaves, int *nleaves) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // per warp: two queue arrays of `cap` entries, the staged batch and its sorted copy
-    PQE *base = reinterpret_cast<PQE *>(smem_raw) + (size_t)w * (2 * cap + 64);
+    unsigned char *mine = smem_raw + (size_t)w * prio_warp_bytes(budget, F.T);
+    PQE *base = reinterpret_cast<PQE *>(mine);
     PQE *qa = base, *qb = base + cap, *stage = base + 2 * cap, *sorted = stage + 32;
+    float *w2s = reinterpret_cast<float *>(base + 2 * cap + 64);
     const int nn = (1 << F.L) - 1;
     const int nwq = blockDim.x >> 5;
     for (long long qi = (long long)blockIdx.x * nwq + w; qi < m; qi += (long long)gridDim.x * nwq) {
@@ -103,12 +110,19 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
         for (int t0 = 0; t0 < F.T; t0 += 32) {
             const int t = t0 + lane;
             const bool act = t < F.T;
+            float w2 = 0.f;
+            if (act && F.U) {  // the query's reflection for this tree (Sec. 2.3)
+                w2 = reflect_w2(F.U + (size_t)t * F.d, q, F.d);
+                w2s[t] = w2;
+            }
             int j = 0;
             for (int l = 0; l < F.L; ++l) {
                 PQE e = pq_inf();
                 if (act) {
                     const int2 nd = __ldg(F.nodes + (size_t)t * F.nnodes + j);
-                    const float qs = __ldg(q + nd.x), v = __int_as_float(nd.y);
+                    const float qx = __ldg(q + nd.x);
+                    const float qs = F.U ? reflect_coord(qx, w2, __ldg(F.U + (size_t)t * F.d + nd.x)) : qx;
+                    const float v = __int_as_float(nd.y);
                     e.key = fabs((double)qs - (double)v);
                     e.tree = t;
                     e.node = qs < v ? 2 * j + 2 : 2 * j + 1;  // the child not taken
@@ -133,9 +147,12 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
             int nb = 0, leaf = 0;
             if (lane == 0) {
                 int j = top.node;
+                const float w2 = F.U ? w2s[top.tree] : 0.f;
                 while (j < nn) {
                     const int2 nd = __ldg(F.nodes + (size_t)top.tree * F.nnodes + j);
-                    const float qs = __ldg(q + nd.x), v = __int_as_float(nd.y);
+                    const float qx = __ldg(q + nd.x);
+                    const float qs = F.U ? reflect_coord(qx, w2, __ldg(F.U + (size_t)top.tree * F.d + nd.x)) : qx;
+                    const float v = __int_as_float(nd.y);
                     PQE e;
                     e.key = fabs((double)qs - (double)v);
                     e.tree = top.tree;
@@ -163,9 +180,7 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
 
 }  // namespace
 
-static size_t prio_warp_bytes(int budget) { return (size_t)(2 * (budget + 32) + 64) * sizeof(PQE); }
-
-size_t gf_prio_smem_bytes(int budget) { return prio_warp_bytes(budget); }
+size_t gf_prio_smem_bytes(int budget, int T) { return prio_warp_bytes(budget, T); }
 
 int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int budget, unsigned *leaves,
                           int *nleaves, cudaStream_t st) {
@@ -173,7 +188,7 @@ int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int bud
     int dev = 0, lim = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t per_warp = prio_warp_bytes(budget);
+    const size_t per_warp = prio_warp_bytes(budget, F->T);
     const int warps = (int)std::min<size_t>(PRIO_WARPS, (size_t)lim / per_warp);
     if (warps < 1) return gf_fail(GF_EUNSUPPORTED, "leaf budget %d needs %zu B of shared memory", budget, per_warp);
     const size_t smem = per_warp * warps;

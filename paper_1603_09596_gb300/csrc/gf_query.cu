@@ -53,6 +53,22 @@ __device__ __forceinline__ int descend_tree(const int2 *__restrict__ nodes, int 
     return j - ((1 << L) - 1);
 }
 
+// Leaf of tree t: the query is reflected first when the forest has Householder vectors (Sec. 2.3:
+// "the query is transformed ... prior to descending"); only the coordinates the path reads are
+// formed.
+__device__ __forceinline__ int descend_tree_t(const ForestView &F, int t, const float *q) {
+    const int2 *nodes = F.nodes + (size_t)t * F.nnodes;
+    if (!F.U) return descend_tree(nodes, F.L, q);
+    const float *u = F.U + (size_t)t * F.d;
+    const float w2 = reflect_w2(u, q, F.d);
+    int j = 0;
+    for (int l = 0; l < F.L; ++l) {
+        const int2 nd = __ldg(nodes + j);
+        j = 2 * j + (reflect_coord(q[nd.x], w2, __ldg(u + nd.x)) < __int_as_float(nd.y) ? 1 : 2);
+    }
+    return j - ((1 << F.L) - 1);
+}
+
 // ---------------------------------------------------------------- block helpers
 
 // Ascending bitonic sort of a[0..P), P a power of two, by the whole block.
@@ -412,7 +428,7 @@ __global__ void k_descend(ForestView F, const float *__restrict__ Q, long long m
     if (g >= m * F.T) return;
     const long long i = g / F.T;
     const int t = (int)(g - i * F.T);
-    leaf[g] = descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, Q + i * F.d);
+    leaf[g] = descend_tree_t(F, t, Q + i * F.d);
 }
 
 // Stage 2: one CTA per query.
@@ -486,7 +502,7 @@ __global__ void k_query_fused(ForestView F, const float *__restrict__ Q, long lo
         load_query(Q + i * F.d, F.d, s.qs);
         __syncthreads();
         for (int t = threadIdx.x; t < F.T; t += blockDim.x)
-            leaf_range(F, t, descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, s.qs), s.lofs, s.lcnt);
+            leaf_range(F, t, descend_tree_t(F, t, s.qs), s.lofs, s.lcnt);
         __syncthreads();
         int C = gather_unique(F, s.lofs, s.lcnt, s.lpos, reinterpret_cast<int *>(s.keys), s.u, s.wtmp,
                               s.sh);
@@ -712,7 +728,7 @@ __global__ void __launch_bounds__(256, 2) k_query_stream(ForestView F, const flo
                 b = (int)(code & ((1u << F.L) - 1u));
             } else {
                 t = j;
-                b = descend_tree(F.nodes + (size_t)t * F.nnodes, F.L, qs);
+                b = descend_tree_t(F, t, qs);
             }
             const long long lo = ((long long)b * F.n) >> F.L;
             const long long hi = ((long long)(b + 1) * F.n) >> F.L;
@@ -820,7 +836,7 @@ constexpr int ORDER_CHUNK = 16384;  // queries sorted together by one CTA
 __global__ void k_order_keys(ForestView F, const float *__restrict__ Q, long long m, unsigned long long *keys) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    const int leaf0 = descend_tree(F.nodes, F.L, Q + i * F.d);
+    const int leaf0 = descend_tree_t(F, 0, Q + i * F.d);
     keys[i] = ((unsigned long long)(unsigned)leaf0 << 32) | (unsigned long long)(i & 0xffffffffll);
 }
 

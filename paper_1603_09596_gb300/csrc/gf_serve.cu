@@ -108,6 +108,8 @@ static int launch_batch(gf_server *S, Slot &s, int f) {
     gf_query_opts_default(&o);
     o.precision = S->opts.precision;
     o.rerank_R = S->opts.rerank_R;
+    o.checks = S->opts.checks;
+    o.eps = S->opts.eps;
     o.stream = s.stream;
     o.algo = GF_ALGO_STREAM;
     o.workspace = s.ws;
@@ -240,6 +242,8 @@ extern "C" int gf_server_create(gf_forest *const *forests, int32_t nforests, con
         gf_query_opts_default(&qo);
         qo.precision = o.precision;
         qo.rerank_R = o.rerank_R;
+        qo.checks = o.checks;
+        qo.eps = o.eps;
         int64_t b = 0;
         int r = gf_query_workspace_size(forests[i], o.max_batch, &qo, &b);
         if (r) { delete S; return r; }

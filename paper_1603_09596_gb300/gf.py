@@ -45,7 +45,7 @@ class QueryOpts(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("slots", C.c_int32), ("hbm_budget_bytes", C.c_int64),
                 ("k_max", C.c_int32), ("precision", C.c_int32), ("rerank_R", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("checks", C.c_int32), ("eps", C.c_double)]
 
 
 class ServerStats(C.Structure):
@@ -77,6 +77,8 @@ def lib() -> C.CDLL:
         sig = {
             "gf_build": ([P, i64, i32, i32, i32, P, u64, P], i32),
             "gf_build_ex": ([P, i64, i32, i32, i32, P, u64, i32, P, P], i32),
+            "gf_build_reflected": ([P, i64, i32, i32, i32, P, u64, P, i32, P, P], i32),
+            "gf_forest_set_reflections": ([P, P], i32),
             "gf_forest_import": ([P, i64, i32, i32, i32, P, P, P, P], i32),
             "gf_forest_export": ([P, P, P, P], i32),
             "gf_forest_get_info": ([P, P], i32),
@@ -168,12 +170,23 @@ def gf_rand_params(t: int = 5, shuffle: int = 1, var_scope: int = GF_VAR_NODE,
 
 def gf_build(X: torch.Tensor, T: int, leaf_size: int, t: int = 5, shuffle: int = 1,
              var_scope: int = GF_VAR_NODE, seed: int = 0, householder: int = 0,
-             borrow_x: bool = False, stream=None) -> Forest:
+             borrow_x: bool = False, stream=None, U=None) -> Forest:
+    """Build a forest on the GPU; with U (host [T, d] float32) every tree is built on its
+    Householder-reflected points (gf_build_reflected)."""
     n, d = X.shape
-    rp = gf_rand_params(t, shuffle, var_scope, householder)
+    rp = gf_rand_params(t, shuffle, var_scope, 1 if U is not None else householder)
     h = C.c_void_p()
-    _check(lib().gf_build_ex(_dptr(X, torch.float32, "X"), n, d, T, leaf_size, C.byref(rp),
-                             seed & (2**64 - 1), int(borrow_x), _stream(stream), C.byref(h)))
+    if U is not None:
+        import numpy as np
+        Uh = np.ascontiguousarray(U, dtype=np.float32)
+        if Uh.shape != (T, d):
+            raise ValueError("U must be [T, d]")
+        _check(lib().gf_build_reflected(_dptr(X, torch.float32, "X"), n, d, T, leaf_size, C.byref(rp),
+                                        seed & (2**64 - 1), Uh.ctypes.data, int(borrow_x), _stream(stream),
+                                        C.byref(h)))
+    else:
+        _check(lib().gf_build_ex(_dptr(X, torch.float32, "X"), n, d, T, leaf_size, C.byref(rp),
+                                 seed & (2**64 - 1), int(borrow_x), _stream(stream), C.byref(h)))
     f = Forest(h)
     if borrow_x:
         f._x = X  # keep the borrowed points alive
@@ -190,6 +203,12 @@ def gf_forest_import(X: torch.Tensor, T: int, leaf_size: int, split_dim, split_v
     _check(lib().gf_forest_import(_dptr(X, torch.float32, "X"), n, d, T, leaf_size,
                                   sd.ctypes.data, sv.ctypes.data, pm.ctypes.data, C.byref(h)))
     return Forest(h)
+
+
+def gf_forest_set_reflections(F: Forest, U) -> None:
+    import numpy as np
+    Uh = np.ascontiguousarray(U, dtype=np.float32)
+    _check(lib().gf_forest_set_reflections(F.handle, Uh.ctypes.data))
 
 
 def gf_forest_export(F: Forest):
@@ -300,10 +319,11 @@ class Server:
     """Continuous-batching request loop over resident forests (gf_server_* in the C ABI)."""
 
     def __init__(self, forests, max_batch: int = 1024, slots: int = 4, hbm_budget_bytes: int = 4 << 30,
-                 k_max: int = 10, precision: int = GF_FP32, rerank_R: int = 0):
+                 k_max: int = 10, precision: int = GF_FP32, rerank_R: int = 0, checks: int = 0,
+                 eps: float = 0.0):
         self.forests = list(forests)      # keep the forests alive while the server runs
         arr = (C.c_void_p * len(self.forests))(*[f.handle for f in self.forests])
-        o = ServerOpts(max_batch, slots, hbm_budget_bytes, k_max, precision, rerank_R, 0)
+        o = ServerOpts(max_batch, slots, hbm_budget_bytes, k_max, precision, rerank_R, checks, eps)
         self.handle = C.c_void_p()
         _check(lib().gf_server_create(arr, len(self.forests), C.byref(o), C.byref(self.handle)))
         self.dims = [f.info.d for f in self.forests]

@@ -115,8 +115,8 @@ def test_build_rejects_bad_input(gf):
         gf.gf_build(Xg, 2, 4, t=9)
     assert e.value.code == gf.GF_EINVAL
     with pytest.raises(gf.GFError) as e:
-        gf.gf_build(Xg, 2, 4, householder=1)
-    assert e.value.code == gf.GF_EUNSUPPORTED
+        gf.gf_build(Xg, 2, 4, householder=1)          # reflections need their vectors
+    assert e.value.code == gf.GF_EINVAL
     Xn = Xg.clone()
     Xn[7, 3] = float("nan")
     with pytest.raises(gf.GFError) as e:
@@ -136,3 +136,32 @@ def test_build_recall_matches_oracle_forest(gf):
     rg = oracle.recall_at_1(gi.cpu().numpy(), ed, X, Q)
     ro = oracle.recall_at_1(oi, ed, X, Q)
     assert abs(rg - ro) <= 0.005, (rg, ro)
+
+
+# ---------------------------------------------------------------- Householder reflections (Sec. 2.2)
+
+def _units(T, d, seed):
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((T, d))
+    return (U / np.linalg.norm(U, axis=1, keepdims=True)).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,d,T,p", [(10_000, 64, 4, 32), (30_000, 37, 3, 16), (3000, 300, 2, 40)])
+def test_reflected_build_matches_oracle(gf, n, d, T, p):
+    X, _ = synth.mixture(n, d, 1, "B", seed=n + 1)
+    U = _units(T, d, n)
+    G = gf.gf_build(torch.from_numpy(X).cuda(), T, p, seed=4, U=U)
+    sd, sv, pm = gf.gf_forest_export(G)
+    inf = G.info
+    Fg = oracle.Forest(inf.n, inf.d, inf.T, inf.leaf_size, inf.L, sd, sv, pm, U)
+    Fo = oracle.build_forest(X, T, p, seed=4, U=U)
+    assert np.array_equal(Fg.split_dim, Fo.split_dim)
+    assert np.array_equal(Fg.split_val, Fo.split_val)
+    assert np.array_equal(Fg.perm, Fo.perm)
+
+
+def test_reflected_global_scope_is_rejected(gf):
+    X, _ = synth.mixture(500, 8, 1, "A", seed=2)
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_build(torch.from_numpy(X).cuda(), 2, 16, var_scope=gf.GF_VAR_GLOBAL, U=_units(2, 8, 1))
+    assert e.value.code == gf.GF_EINVAL

@@ -407,3 +407,63 @@ def test_configure_meets_recall_target(gf):
                              grid=[(8, 32, 0), (16, 64, 0), (16, 64, 64), (32, 256, 0)])
     assert res["met_target"] and res["choice"]["recall_at_1"] >= 0.9
     assert len(res["tried"]) == 4
+
+
+# ---------------------------------------------------------------- Householder reflections (Sec. 2.2)
+
+def _units(T, d, seed):
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((T, d))
+    return (U / np.linalg.norm(U, axis=1, keepdims=True)).astype(np.float32)
+
+
+_refl = {}
+
+
+def reflected_case(name):
+    if name not in _refl:
+        X, Q, F0 = case(name)
+        U = _units(F0.T, F0.d, 77)
+        _refl[name] = (X, Q, oracle.build_forest(X, F0.T, F0.leaf_size, t=min(5, F0.d), seed=7, U=U), U)
+    return _refl[name]
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "gist_like"])
+def test_reflected_descent_and_candidates_bit_exact(gf, name):
+    X, Q, F, U = reflected_case(name)
+    G, _ = gpu_forest(gf, X, F)
+    gf.gf_forest_set_reflections(G, U)
+    Qg = torch.from_numpy(Q).cuda()
+    leaf = gf.gf_descend(G, Qg).cpu().numpy()
+    assert np.array_equal(leaf, oracle.descend(F, Q))
+    nc = torch.empty(Q.shape[0], dtype=torch.int32, device="cuda")
+    gf.gf_query(G, Qg, 1, algo=gf.GF_ALGO_STREAM, ncand_out=nc)
+    offs, _ = oracle.candidates(F, leaf)
+    assert np.array_equal(nc.cpu().numpy(), np.diff(offs))
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "gist_like"])
+@pytest.mark.parametrize("algo", ["sort", "stream"])
+def test_reflected_query_matches_oracle(gf, name, algo):
+    X, Q, F, U = reflected_case(name)
+    G, _ = gpu_forest(gf, X, F)
+    gf.gf_forest_set_reflections(G, U)
+    a = gf.GF_ALGO_SORT if algo == "sort" else gf.GF_ALGO_STREAM
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, algo=a)
+    oi, od = oracle.search(F, X, Q, 10)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+
+
+@pytest.mark.parametrize("name,c", [("tiny", 24), ("gist_like", 48)])
+def test_reflected_priority_search_matches_oracle(gf, name, c):
+    X, Q, F, U = reflected_case(name)
+    G, _ = gpu_forest(gf, X, F)
+    gf.gf_forest_set_reflections(G, U)
+    Qg = torch.from_numpy(Q).cuda()
+    leaves, nl = gf.gf_prio_leaves(G, Qg, c)
+    oi, od, onc, onl, oseq = oracle.search_priority(F, X, Q, 10, c, return_leaves=True)
+    leaves = leaves.cpu().numpy().view(np.uint32).astype(np.int64)
+    for i in range(Q.shape[0]):
+        assert np.array_equal(leaves[i, :onl[i]], oseq[i, :onl[i]])
+    gi, gd = gf.gf_query(G, Qg, 10, checks=c)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)

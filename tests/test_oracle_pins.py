@@ -343,3 +343,62 @@ def test_priority_pop_order_across_trees(golden_dir):
     for c, cand in g["candidates_after_c"].items():
         _, _, nc, nl = oracle.search_priority(F, X, q, 1, int(c))
         assert (nl[0], nc[0]) == (int(c), cand)
+
+
+# ------------------------------------------------------------------ Householder reflection (Sec. 2.2)
+
+def _units(T, d, seed):
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((T, d))
+    return (U / np.linalg.norm(U, axis=1, keepdims=True)).astype(np.float32)
+
+
+def test_reflection_basis_vector_flips_one_coordinate():
+    x = np.float32([1.5, -2.25, 3.0, 0.5])
+    u = np.float32([0, 0, 1, 0])
+    assert oracle.reflect(x, u).tolist() == [1.5, -2.25, -3.0, 0.5]
+
+
+def test_reflection_is_an_involutive_isometry():
+    rng = np.random.default_rng(31)
+    u = _units(1, 50, 32)[0]
+    x, y = rng.standard_normal((2, 50)).astype(np.float32)
+    px, py = oracle.reflect(x, u), oracle.reflect(y, u)
+    # float32 arithmetic: within a few units of rounding of the exact reflection
+    np.testing.assert_allclose(oracle.reflect(px, u), x, atol=1e-4)
+    assert np.linalg.norm(px - py) == pytest.approx(np.linalg.norm(x - y), rel=1e-4)
+    assert np.dot(px.astype(np.float64), u) == pytest.approx(-np.dot(x.astype(np.float64), u), abs=1e-4)
+
+
+def test_reflected_tree_is_the_tree_of_reflected_points():
+    X, _ = synth.mixture(900, 10, 1, "B", seed=33)
+    U = _units(3, 10, 34)
+    F = oracle.build_forest(X, 3, 20, seed=5, U=U)
+    for t in range(3):
+        Xt = np.stack([oracle.reflect(x, U[t]) for x in X])
+        Ft = oracle.build_forest(Xt, 3, 20, seed=5)
+        assert np.array_equal(F.split_dim[t], Ft.split_dim[t])
+        assert np.array_equal(F.split_val[t], Ft.split_val[t])
+        assert np.array_equal(F.perm[t], Ft.perm[t])
+
+
+def test_reflected_forest_data_point_reaches_its_leaf():
+    # queries are reflected before descending (Sec. 2.3) with the same arithmetic as the points
+    X, _ = synth.mixture(1000, 16, 1, "B", seed=35)
+    U = _units(4, 16, 36)
+    F = oracle.build_forest(X, 4, 30, seed=2, U=U)
+    leaf = oracle.descend(F, X)
+    for tr in range(F.T):
+        for b in range(1 << F.L):
+            lo, hi = F.leaf_range(b)
+            for i in F.perm[tr, lo:hi]:
+                assert leaf[i, tr] == b
+
+
+def test_reflected_single_leaf_is_exact_on_original_distances():
+    X, Q = synth.mixture(200, 8, 15, "A", seed=37)
+    F = oracle.build_forest(X, 2, 200, seed=0, U=_units(2, 8, 38))
+    ids, d = oracle.search(F, X, Q, 5)
+    ei, ed = oracle.bruteforce(X, Q, 5)
+    assert np.array_equal(ids, ei)
+    np.testing.assert_allclose(d, ed, rtol=1e-12)
