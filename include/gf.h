@@ -67,6 +67,12 @@ typedef struct gf_rand_params {
                             8 * next_pow2(T * max_leaf) bytes of shared memory per CTA */
 #define GF_ALGO_STREAM 2 /* candidates de-duplicated through a per-CTA bitmap over the point ids
                             in device memory ("seen" array, Sec. 2.3); any candidate count */
+#define GF_ALGO_LEAF 3   /* leaf-major batch (bf16 screen, one leaf per tree): the (query, tree)
+                            pairs are grouped by the leaf they reach, each leaf's rows are read once
+                            per group of up to 32 queries and scored against all of them on the
+                            tensor cores; per query the trees' shortlists are merged, de-duplicated
+                            by id and reranked in float32.  R <= 64, T * R <= 8192,
+                            T * 2^L <= 2^22; the workspace need not be zero and is left zero */
 
 /* Order in which the streaming kernel's CTAs take the queries of a batch.  Results do not depend
  * on it; throughput does: queries that reach the same leaf of tree 0 share most candidates, and
@@ -222,6 +228,11 @@ int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_t k, const 
  * ceil(n / 32) words per CTA of the launch, plus 12 bytes per query when the batch is reordered
  * (GF_ORDER_*).  An upper bound for every k.  o may be NULL for the defaults. */
 int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_query_opts *o, int64_t *bytes);
+
+/* The first error a library kernel recorded on the current device since the last call, 0 if none
+ * (a bounded wait that ran out records GF_ETIMEOUT); clears it.  Synchronizes the device.  The
+ * paper has no counterpart.  Errors: GF_EINVAL (null pointer), GF_ECUDA. */
+int gf_kernel_status(int32_t *status);
 
 /* ---------------------------------------------------------------- query without allocation
  * gf_query_noalloc -- the query of gf_query_ex with GF_ALGO_STREAM, for callers that may not

@@ -67,6 +67,7 @@ static void forest_release(gf_forest *F) {
     cudaFree(F->nodes);
     cudaFree(F->perm);
     cudaFree(F->xb);
+    cudaFree(F->xbn);
     cudaFree(F->x8);
     cudaFree(F->scale8);
     cudaFree(F->U);
@@ -296,6 +297,21 @@ __global__ void k_to_fp8(const float *__restrict__ x, int ldx, long long n, int 
     }
 }
 
+// xbn[i] = sum_j xb[i][j]^2, accumulated in float64 and rounded once: a warp per row.
+__global__ void k_bf16_sqnorm(const __nv_bfloat16 *__restrict__ xb, long long n, int ldb, float *xbn) {
+    const int lane = threadIdx.x & 31;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += ((long long)gridDim.x * blockDim.x) >> 5) {
+        double acc = 0.0;
+        for (int j = lane; j < ldb; j += 32) {
+            const double v = (double)__bfloat162float(xb[i * ldb + j]);
+            acc += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) xbn[i] = (float)acc;
+    }
+}
+
 extern "C" int gf_forest_add_screen(gf_forest *F, int32_t precision, void *stream) {
     if (!F) return gf_fail(GF_EINVAL, "null forest");
     cudaStream_t st = (cudaStream_t)stream;
@@ -303,8 +319,10 @@ extern "C" int gf_forest_add_screen(gf_forest *F, int32_t precision, void *strea
     if (precision == GF_BF16_RERANK) {
         if (F->xb) return GF_OK;
         if ((r = gf_dmalloc((void **)&F->xb, (size_t)F->n * F->ldb * 2))) return r;
+        if ((r = gf_dmalloc((void **)&F->xbn, (size_t)F->n * 4))) { cudaFree(F->xb); F->xb = nullptr; return r; }
         k_to_bf16<<<F->num_sms * 8, 256, 0, st>>>(F->x, F->ldx, F->n, F->d, F->ldb, F->xb);
-        F->device_bytes += (int64_t)F->n * F->ldb * 2;
+        k_bf16_sqnorm<<<F->num_sms * 8, 256, 0, st>>>(F->xb, F->n, F->ldb, F->xbn);
+        F->device_bytes += (int64_t)F->n * F->ldb * 2 + F->n * 4;
     } else if (precision == GF_FP8_RERANK) {
         if (F->x8) return GF_OK;
         if ((r = gf_dmalloc((void **)&F->x8, (size_t)F->n * F->ld8))) return r;
@@ -340,7 +358,7 @@ extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_
     const int warps = o->warps_per_cta > 0 ? o->warps_per_cta : F->tune_warps[p];
     if (warps > 32) return gf_fail(GF_EINVAL, "warps_per_cta=%d > 32", warps);
     const int cps = o->ctas_per_sm > 0 ? o->ctas_per_sm : F->tune_ctas[p];
-    if (o->algo < GF_ALGO_AUTO || o->algo > GF_ALGO_STREAM) return gf_fail(GF_EINVAL, "unknown algo %d", o->algo);
+    if (o->algo < GF_ALGO_AUTO || o->algo > GF_ALGO_LEAF) return gf_fail(GF_EINVAL, "unknown algo %d", o->algo);
     QueryExtra x;
     x.algo = o->algo;
     x.workspace = o->workspace;
@@ -378,7 +396,18 @@ extern "C" int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_q
     int r = gf_stream_grid(F, m, warps, cps, p, 1, R, &grid);
     if (r) return r;
     const bool ordered = o->order == GF_ORDER_LOCALITY || (o->order == GF_ORDER_AUTO && m > grid);
-    return gf_stream_workspace_bytes(F, m, grid, ordered, leaf_budget_of(F, o->checks, o->eps), bytes);
+    if ((r = gf_stream_workspace_bytes(F, m, grid, ordered, leaf_budget_of(F, o->checks, o->eps), bytes))) return r;
+    if (o->algo == GF_ALGO_LEAF || o->algo == GF_ALGO_AUTO) {
+        // the leaf-major path's scratch; AUTO gets the larger of the two
+        QueryExtra x;
+        x.leaf_budget = leaf_budget_of(F, o->checks, o->eps);
+        x.ncand_out = o->ncand_out;
+        const bool leaf_ok = gf_leaf_unsupported(F, m, 1, p, R, x) == nullptr;
+        const int64_t lb = gf_leaf_workspace_bytes(F, m, R, o->order);
+        if (o->algo == GF_ALGO_LEAF) *bytes = lb;
+        else if (leaf_ok && gf_leaf_preferred(F, m, 1, p, R, x)) *bytes = std::max(*bytes, lb);
+    }
+    return GF_OK;
 }
 
 extern "C" int gf_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int64_t *ids,

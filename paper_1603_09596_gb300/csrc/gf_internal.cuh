@@ -17,6 +17,7 @@
 //   nodes   int2  [T][2^L - 1]    internal nodes in heap order: .x split dim, .y split value bits
 //   perm    int32 [T][n]          leaf permutation of every tree (leaf b = [b n >> L, (b+1) n >> L))
 //   xb      bf16  [n][ldb]        optional screening copy, ldb = round_up(d, 8)
+//   xbn     float [n]             |xb_i|^2 (float64 sum rounded once), with xb
 //   x8      e4m3  [n][ld8]        optional screening copy, ld8 = round_up(d, 16)
 //   scale8  float [n]             per-row scale of x8
 struct gf_forest {
@@ -29,6 +30,7 @@ struct gf_forest {
     int2 *nodes = nullptr;
     int32_t *perm = nullptr;
     __nv_bfloat16 *xb = nullptr;
+    float *xbn = nullptr;
     uint8_t *x8 = nullptr;
     float *scale8 = nullptr;
     float *U = nullptr;  // [T][d] Householder vectors (Sec. 2.2), or null: trees on X itself
@@ -46,6 +48,7 @@ struct gf_forest {
 struct ForestView {
     const float *x;
     const __nv_bfloat16 *xb;
+    const float *xbn;
     const uint8_t *x8;
     const float *scale8;
     const float *U;  // [T][d] or null
@@ -57,7 +60,7 @@ struct ForestView {
 
 inline ForestView view_of(const gf_forest *F) {
     ForestView v;
-    v.x = F->x; v.xb = F->xb; v.x8 = F->x8; v.scale8 = F->scale8; v.U = F->U;
+    v.x = F->x; v.xb = F->xb; v.xbn = F->xbn; v.x8 = F->x8; v.scale8 = F->scale8; v.U = F->U;
     v.nodes = F->nodes; v.perm = F->perm;
     v.n = F->n; v.d = F->d; v.ldx = F->ldx; v.ldb = F->ldb; v.ld8 = F->ld8;
     v.T = F->T; v.L = F->L; v.nnodes = (1 << F->L) - 1;
@@ -133,6 +136,16 @@ inline int32_t leaf_budget_of(const gf_forest *F, int32_t checks, double eps) {
     while ((double)nl < budget) ++nl;  // the same comparison the search loop makes
     return nl > F->T ? (int32_t)nl : 0;
 }
+
+// Leaf-major batched path (GF_ALGO_LEAF): the bf16 screen of one-leaf-per-tree queries.
+int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int32_t order,
+                   cudaStream_t st, int64_t *ids, float *dists, void *workspace, int64_t workspace_bytes);
+int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t R, int32_t order);
+// Whether GF_ALGO_AUTO takes the leaf-major path for this batch.
+bool gf_leaf_preferred(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R, const QueryExtra &x);
+// Why the leaf-major path cannot run this query (nullptr: it can).
+const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R,
+                                const QueryExtra &x);
 
 int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision,
                     int32_t R, int32_t warps, int32_t ctas_per_sm, cudaStream_t s, int64_t *ids,

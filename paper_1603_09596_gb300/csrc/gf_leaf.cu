@@ -1,0 +1,772 @@
+// gf_leaf.cu -- the leaf-major batched query path (GF_ALGO_LEAF): the bf16 screen + float32 rerank
+// of the one-leaf-per-tree search (Alg. 2 with c = T), regrouped so that every leaf's points are
+// read once per group of queries that reach it.
+//
+// A query's candidates are the points of the T leaves it reaches (Eq. 1); its answer is the k
+// nearest of their union.  In a large batch many queries reach the same leaf of a tree (10^4
+// queries over 2^10 leaves: about ten each), and a per-query kernel reads that leaf's rows once per
+// query.  Here:
+//   1. descend: leaf[q][t] for every (query, tree);
+//   2. bucket the (query, tree) pairs by (tree, leaf) (counting sort);
+//   3. cut every bucket into chunks of at most NQ queries and order the chunks by the smallest
+//      tree-0 leaf among their queries, so chunks of different trees that cover the same region of
+//      the data run at about the same time and find each other's rows in L2;
+//   4. score (k_leaf_score): one persistent CTA per SM walks the chunks.  A chunk's leaf rows are
+//      staged in shared memory 128 at a time and multiplied against the chunk's queries on the
+//      tensor cores (tcgen05.mma, bf16 inputs, float32 accumulators in tensor memory).  The screened
+//      score of point x for query q is |x~|^2 - 2 x~.q, which orders the points of one query as
+//      |x~ - q|^2 does (the two differ by |q|^2).  x~ is the bf16 copy of the forest; the query
+//      enters as two bf16 parts hi + lo (hi = bf16(q), lo = bf16(q - hi)), i.e. with about 16
+//      significant bits, so the screen is the distance to the bf16 points, as in the other kernels.
+//      Each (query, tree) keeps the R best (score, id) keys of its leaf;
+//   5. merge (k_leaf_merge): per query the T lists are de-duplicated by id, the R best screened
+//      ids are rescored in float32 (direct form, the same code as the other kernels' rerank) and
+//      the k nearest are written in (distance, id) order.
+// Results are those of the screened search of the other kernels: the screen ranks the query's
+// candidate union, its R best are rescored exactly.  Screen scores near the shortlist boundary can
+// order differently from another kernel's screen (different float32 rounding), as between any two
+// screens.
+//
+// Waits on mbarriers are bounded (about two seconds).  A wait that runs out records
+// GF_ETIMEOUT in a device status word (gf_kernel_status reads it), and every role of the CTA leaves
+// its loop, lets its copies and tensor-core operations complete and frees its tensor memory.
+#include "gf_internal.cuh"
+#include "gf_device.cuh"
+#include "gf_score.cuh"
+
+#include <algorithm>
+#include <climits>
+
+__device__ int g_kernel_status = 0;  // first error a kernel of the library recorded
+
+namespace {
+
+constexpr int NQ = 32;           // queries per chunk: the MMA's N
+constexpr int BM = 128;          // leaf rows per tile: the MMA's M, one tensor-memory lane each
+constexpr int BK = 64;           // bf16 values per k-step: one 128-byte swizzled row
+constexpr int STAGES = 5;        // shared-memory pipeline depth
+constexpr int LAG = 3;           // stages a producer thread keeps in flight before it signals one
+constexpr int R_MAX = 64;        // longest shortlist per (query, tree)
+constexpr int CAP = 256;         // per-query key buffer of the epilogue
+constexpr int A_BYTES = BM * 128;
+constexpr int B_BYTES = NQ * 128;
+constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // leaf rows, query hi, query lo
+constexpr int TMEM_COLS = 2 * NQ;                   // two accumulators of NQ float32 columns
+constexpr int EPI_THREADS = 128, PROD_THREADS = 128;
+constexpr int THREADS = EPI_THREADS + PROD_THREADS + 32;
+constexpr int MAX_KEYS = 8192;                      // T * R limit of the merge
+static_assert(STAGE_BYTES % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
+static_assert(LAG < STAGES, "a producer must signal a stage before it needs it again");
+
+// shared-memory plan of k_leaf_score (offsets from a 1024-aligned base)
+constexpr int SM_STAGES = 0;
+constexpr int SM_BUFQ = SM_STAGES + STAGES * STAGE_BYTES;
+constexpr int SM_TAU = SM_BUFQ + NQ * CAP * 8;
+constexpr int SM_CNT = SM_TAU + NQ * 8;
+constexpr int SM_QID = SM_CNT + NQ * 4;
+constexpr int SM_BAR = SM_QID + NQ * 4;  // full[STAGES] empty[STAGES] dfull[2] dempty[2] fin
+constexpr int SM_MISC = SM_BAR + (2 * STAGES + 5) * 8;  // tensor-memory base, abort flag
+constexpr int SM_TOTAL = SM_MISC + 16;
+constexpr int SMEM_BYTES = SM_TOTAL + 1024;  // slack for aligning the base
+
+// ---------------------------------------------------------------- PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after about two seconds
+
+// Wait for the phase of `parity` to complete.  Returns false (and raises the CTA's abort flag and
+// the device status) if it did not within WAIT_NS, or if another role of the CTA aborted.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t spin = 1;; ++spin) {
+        if (mbar_test(bar, parity)) return true;
+        if ((spin & 255) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                atomicCAS(&g_kernel_status, 0, GF_ETIMEOUT);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+}
+
+// 16-byte global -> shared copy that reads `bytes` (0..16) bytes and zero-fills the rest
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// make this thread's completed generic-proxy shared-memory writes visible to the tensor cores
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzled layout: rows
+// of 128 bytes (64 bf16), 16-byte chunk c of row r stored at chunk c ^ (r % 8), groups of 8 rows
+// 1024 bytes apart; the tile starts on a 1024-byte boundary.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused by this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with bf16 A and B, float32 D, both K-major, M = BM, N = NQ.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NQ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+// arrive on `bar` once every tensor-core operation this thread issued so far has completed
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive float32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory"); }
+
+// barrier of the epilogue threads that also returns whether any of them passed `v` true, so that
+// all of them take the same branch after it
+__device__ __forceinline__ bool epi_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(EPI_THREADS)
+        : "memory");
+    return r != 0;
+}
+
+// float -> unsigned with the same order (negative values below positive ones)
+__device__ __forceinline__ uint32_t ord_f32(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// ---------------------------------------------------------------- warp sort of a key buffer
+
+// Sort a[0..cnt) ascending (cnt <= CAP) by one warp; positions cnt..P-1 become KEY_NONE.
+__device__ void warp_sort_keys(unsigned long long *a, int cnt) {
+    const int lane = threadIdx.x & 31;
+    int P = 2;
+    while (P < cnt) P <<= 1;
+    for (int i = cnt + lane; i < P; i += 32) a[i] = KEY_NONE;
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < (P >> 1); i += 32) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const unsigned long long x = a[lo], y = a[hi];
+                if ((x > y) == ((lo & size) == 0)) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- the scoring kernel
+
+struct LeafArgs {
+    const int2 *items;     // (bucket, first query of the chunk)
+    const int *nitems;     // device count of items
+    const int *bcnt;       // queries per bucket
+    const int *boff;       // first position of each bucket in qlist
+    const int *qlist;      // query ids grouped by bucket
+    const __nv_bfloat16 *qhi, *qlo;  // [m][ldb] query parts
+    unsigned long long *part;        // [m][T][R] screened keys
+    int R;
+};
+
+__device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A, int w, int &t, long long &lo,
+                                         int &rows, int &q0pos, int &nq) {
+    const int2 it = A.items[w];
+    const int u = it.x;
+    t = u >> F.L;
+    const int b = u & ((1 << F.L) - 1);
+    lo = ((long long)b * F.n) >> F.L;
+    rows = (int)((((long long)(b + 1) * F.n) >> F.L) - lo);
+    q0pos = A.boff[u] + it.y;
+    nq = min(NQ, A.bcnt[u] - it.y);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned long long *bufq = reinterpret_cast<unsigned long long *>(sm + SM_BUFQ);
+    unsigned long long *tau = reinterpret_cast<unsigned long long *>(sm + SM_TAU);
+    int *cnt = reinterpret_cast<int *>(sm + SM_CNT);
+    int *qid_s = reinterpret_cast<int *>(sm + SM_QID);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + SM_BAR);
+    uint64_t *empty = full + STAGES;
+    uint64_t *dfull = empty + STAGES;
+    uint64_t *dempty = dfull + 2;
+    uint64_t *fin = dempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + SM_MISC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + SM_MISC + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, PROD_THREADS);
+            mbar_init(empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(dfull + b, 1);
+            mbar_init(dempty + b, EPI_THREADS);
+        }
+        mbar_init(fin, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {  // the MMA warp owns the tensor memory
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int nitems = *A.nitems;
+    const int KC = (F.d + BK - 1) / BK;
+    const uint32_t stage0 = smem_u32(sm + SM_STAGES);
+
+    if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------ producers: leaf rows and query parts
+        const int pt = tid - EPI_THREADS;
+        const int c = pt & 7, rsub = pt >> 3;  // 16-byte column chunk, first row
+        uint32_t it = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+            int t, rows, q0pos, nq;
+            long long lo;
+            chunk_of(F, A, w, t, lo, rows, q0pos, nq);
+            int qid[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int j = rsub + 16 * i;
+                qid[i] = j < nq ? A.qlist[q0pos + j] : -1;
+            }
+            const int MT = (rows + BM - 1) / BM;
+            for (int mt = 0; mt < MT && ok; ++mt) {
+                int id[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = mt * BM + rsub + 16 * i;
+                    id[i] = r < rows ? __ldg(F.perm + (size_t)t * F.n + lo + r) : -1;
+                }
+                for (int kc = 0; kc < KC; ++kc) {
+                    const uint32_t s = it % STAGES;
+                    if (!mbar_wait(empty + s, ((it / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    const int col = kc * BK + c * 8;
+                    const int nb = max(0, min(16, (F.d - col) * 2));
+                    const uint32_t sa = stage0 + s * STAGE_BYTES;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int r = rsub + 16 * i;
+                        const bool live = id[i] >= 0 && nb > 0;
+                        const __nv_bfloat16 *src = live ? F.xb + (size_t)id[i] * F.ldb + col : F.xb;
+                        cp_async16(sa + r * 128 + ((c ^ (r & 7)) << 4), src, live ? nb : 0);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const __nv_bfloat16 *qb = h ? A.qlo : A.qhi;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int j = rsub + 16 * i;
+                            const bool live = qid[i] >= 0 && nb > 0;
+                            const __nv_bfloat16 *src = live ? qb + (size_t)qid[i] * F.ldb + col : qb;
+                            cp_async16(sa + A_BYTES + h * B_BYTES + j * 128 + ((c ^ (j & 7)) << 4), src, live ? nb : 0);
+                        }
+                    }
+                    cp_async_commit();
+                    if (it >= LAG) {
+                        cp_async_wait<LAG>();
+                        fence_proxy_async();
+                        mbar_arrive(full + (it - LAG) % STAGES);
+                    }
+                    ++it;
+                }
+            }
+        }
+        cp_async_wait<0>();
+        fence_proxy_async();
+        if (ok)
+            for (uint32_t j = it >= LAG ? it - LAG : 0; j < it; ++j) mbar_arrive(full + j % STAGES);
+    } else if (warp == 8) {
+        // ------------------------------------------------ MMA issue (one thread)
+        if (lane == 0) {
+            uint32_t it = 0, tile = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+                int t, rows, q0pos, nq;
+                long long lo;
+                chunk_of(F, A, w, t, lo, rows, q0pos, nq);
+                const int MT = (rows + BM - 1) / BM;
+                for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
+                    const uint32_t buf = tile & 1;
+                    if (!mbar_wait(dempty + buf, ((tile >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + buf * NQ;
+                    for (int kc = 0; kc < KC; ++kc, ++it) {
+                        const uint32_t s = it % STAGES;
+                        if (!mbar_wait(full + s, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = stage0 + s * STAGE_BYTES;
+                        const uint64_t da = sdesc_sw128(sa);
+                        const uint64_t dh = sdesc_sw128(sa + A_BYTES);
+                        const uint64_t dl = sdesc_sw128(sa + A_BYTES + B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {  // 16 bf16 (32 bytes) per instruction
+                            mma_bf16(d_tmem, da + 2 * kk, dh + 2 * kk, (kc | kk) != 0);
+                            mma_bf16(d_tmem, da + 2 * kk, dl + 2 * kk, 1u);
+                        }
+                        mma_commit(empty + s);
+                    }
+                    if (!ok) break;
+                    mma_commit(dfull + buf);
+                }
+            }
+            // every issued operation has completed before the tensor memory is freed
+            mma_commit(fin);
+            volatile int no_abort = 0;
+            mbar_wait(fin, 0, &no_abort);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue: screened keys, R best per query
+        const int et = tid;  // tile row and tensor-memory lane
+        uint32_t tile = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+            int t, rows, q0pos, nq;
+            long long lo;
+            chunk_of(F, A, w, t, lo, rows, q0pos, nq);
+            if (et < NQ) {
+                cnt[et] = 0;
+                tau[et] = KEY_NONE;
+                qid_s[et] = et < nq ? A.qlist[q0pos + et] : -1;
+            }
+            epi_sync();
+            const int MT = (rows + BM - 1) / BM;
+            for (int mt = 0; mt < MT; ++mt, ++tile) {
+                const int r = mt * BM + et;
+                const bool valid = r < rows;
+                const int id = valid ? __ldg(F.perm + (size_t)t * F.n + lo + r) : 0;
+                const float xn = valid ? __ldg(F.xbn + id) : 0.f;
+                const uint32_t buf = tile & 1;
+                float v[32];
+                if (!mbar_wait(dfull + buf, (tile >> 1) & 1, abort_flag)) ok = false;
+                if (ok) {
+                    tc_fence_after();
+                    tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * NQ, v);
+                    tc_fence_before();
+                    mbar_arrive(dempty + buf);
+                }
+                if (epi_any(!ok)) {
+                    ok = false;
+                    break;
+                }
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) {
+                    if (j < nq) {
+                        const float s = fmaf(-2.f, v[j], xn);
+                        const unsigned long long key =
+                            valid ? (((unsigned long long)ord_f32(s) << 32) | (unsigned)id) : KEY_NONE;
+                        const bool pass = key < tau[j];
+                        const unsigned bl = __ballot_sync(FULL, pass);
+                        if (bl) {
+                            const int leader = __ffs(bl) - 1;
+                            int base = 0;
+                            if (lane == leader) base = atomicAdd(&cnt[j], __popc(bl));
+                            base = __shfl_sync(FULL, base, leader);
+                            if (pass) bufq[j * CAP + base + __popc(bl & ((1u << lane) - 1u))] = key;
+                        }
+                    }
+                }
+                epi_sync();
+                // keep the R best of any buffer that the next tile could overflow
+                for (int j = warp; j < nq; j += 4) {
+                    if (cnt[j] > CAP - BM) {
+                        warp_sort_keys(bufq + j * CAP, cnt[j]);
+                        if (lane == 0) {
+                            cnt[j] = A.R;
+                            tau[j] = bufq[j * CAP + A.R - 1];
+                        }
+                    }
+                }
+                epi_sync();
+            }
+            if (!ok) break;
+            // the chunk is done: each query's R best keys of this tree's leaf
+            for (int j = warp; j < nq; j += 4) {
+                const int c = cnt[j];
+                warp_sort_keys(bufq + j * CAP, c);
+                unsigned long long *out = A.part + ((size_t)qid_s[j] * F.T + t) * A.R;
+                for (int i = lane; i < A.R; i += 32) out[i] = i < c ? bufq[j * CAP + i] : KEY_NONE;
+            }
+            epi_sync();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 8)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(TMEM_COLS)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------- batch regrouping
+
+__global__ void k_bucket_count(const int *__restrict__ leaf, long long pairs, int T, int L, int *bcnt) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= pairs) return;
+    const int t = (int)(g % T);
+    atomicAdd(bcnt + ((size_t)t << L) + leaf[g], 1);
+}
+
+__global__ void k_bucket_fill(const int *__restrict__ leaf, long long pairs, int T, int L,
+                              const int *__restrict__ boff, int *bfill, int *qlist) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= pairs) return;
+    const int t = (int)(g % T);
+    const size_t u = ((size_t)t << L) + leaf[g];
+    qlist[boff[u] + atomicAdd(bfill + u, 1)] = (int)(g / T);
+}
+
+// Order key of a bucket: the smallest tree-0 leaf among its queries (locality), or the bucket
+// itself (tree-major order).
+__device__ __forceinline__ int bucket_key(int u, const int *bcnt, const int *boff, const int *qlist,
+                                          const int *leaf, int T, bool locality) {
+    if (!locality) return u;
+    int key = INT_MAX;
+    for (int i = 0; i < bcnt[u]; ++i) key = min(key, leaf[(size_t)qlist[boff[u] + i] * T]);
+    return key;
+}
+
+__global__ void k_item_count(int nb, const int *__restrict__ bcnt, const int *__restrict__ boff,
+                             const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int locality,
+                             int *kcnt) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nb || bcnt[u] == 0) return;
+    atomicAdd(kcnt + bucket_key(u, bcnt, boff, qlist, leaf, T, locality), (bcnt[u] + NQ - 1) / NQ);
+}
+
+__global__ void k_item_fill(int nb, const int *__restrict__ bcnt, const int *__restrict__ boff,
+                            const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int locality,
+                            const int *__restrict__ koff, int *kfill, int2 *items) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nb || bcnt[u] == 0) return;
+    const int key = bucket_key(u, bcnt, boff, qlist, leaf, T, locality);
+    const int n_it = (bcnt[u] + NQ - 1) / NQ;
+    const int base = koff[key] + atomicAdd(kfill + key, n_it);
+    for (int i = 0; i < n_it; ++i) items[base + i] = make_int2(u, i * NQ);
+}
+
+// Exclusive prefix sum of a[0..N) into off[0..N], off[N] = total; one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan(const int *__restrict__ a, int N, int *off) {
+    __shared__ int part[1024];
+    const int per = (N + 1023) / 1024;
+    const int beg = min(N, threadIdx.x * per), end = min(N, beg + per);
+    int s = 0;
+    for (int i = beg; i < end; ++i) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the thread sums
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+    for (int i = beg; i < end; ++i) {
+        off[i] = run;
+        run += a[i];
+    }
+    if (threadIdx.x == 1023) off[N] = part[1023];
+}
+
+// q -> (hi, lo): hi = bf16(q), lo = bf16(q - hi), zero in the row padding
+__global__ void k_qsplit(const float *__restrict__ Q, long long m, int d, int ldb, __nv_bfloat16 *qhi,
+                         __nv_bfloat16 *qlo) {
+    const long long total = m * ldb;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long i = g / ldb;
+        const int j = (int)(g - i * ldb);
+        const float v = j < d ? Q[i * d + j] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        qhi[g] = h;
+        qlo[g] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// ---------------------------------------------------------------- merge + rerank
+
+// Per query: the T lists of R screened keys -> distinct ids -> the R best -> float32 rerank ->
+// k nearest.  One CTA per query at a time.
+template <int NCF>
+__global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *__restrict__ Q, long long m, int k,
+                                                    int R, const unsigned long long *__restrict__ part,
+                                                    long long *ids, float *dists) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TR = F.T * R;
+    int P = 2;
+    while (P < TR) P <<= 1;
+    unsigned long long *a = reinterpret_cast<unsigned long long *>(smem_raw);
+    unsigned long long *b = a + P;
+    float *qs = reinterpret_cast<float *>(b + P);
+    int *sid = reinterpret_cast<int *>(qs + ldq_of(F.d));
+    __shared__ int nshort;
+    for (long long qi = blockIdx.x; qi < m; qi += gridDim.x) {
+        // (id, score) order brings the copies of an id together, its best score first
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const unsigned long long key = i < TR ? part[qi * TR + i] : KEY_NONE;
+            a[i] = (key << 32) | (key >> 32);
+        }
+        if (threadIdx.x == 0) nshort = 0;
+        block_sort<unsigned long long>(a, P);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const unsigned long long v = a[i];
+            const bool dup = i > 0 && (v >> 32) == (a[i - 1] >> 32);
+            b[i] = dup ? KEY_NONE : ((v << 32) | (v >> 32));
+        }
+        block_sort<unsigned long long>(b, P);
+        for (int i = threadIdx.x; i < R && i < P; i += blockDim.x) {
+            if (b[i] != KEY_NONE) {
+                sid[i] = (int)(unsigned)(b[i] & 0xffffffffu);
+                atomicAdd(&nshort, 1);
+            }
+        }
+        load_query(Q + qi * F.d, F.d, qs);
+        __syncthreads();
+        const int C = nshort;  // the valid keys are a prefix of the sorted list
+        rescore_f32<NCF>(F, qs, sid, C, a);
+        sort_keys(a, C);
+        write_topk(a, C, k, ids + qi * k, dists + qi * k);
+        __syncthreads();
+    }
+}
+
+size_t merge_smem(const gf_forest *F, int R) {
+    int P = 2;
+    while (P < F->T * R) P <<= 1;
+    return (size_t)2 * P * 8 + (size_t)ldq_of(F->d) * 4 + (size_t)R * 4;
+}
+
+// ---------------------------------------------------------------- workspace
+
+struct LeafWorkspace {
+    size_t bcnt, bfill, kcnt, kfill, zero_end;  // counters, zeroed by every call
+    size_t boff, koff, leaf, qlist, items, qhi, qlo, part, total;
+};
+
+LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int R, int order) {
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t nb = (size_t)F->T << F->L;
+    const size_t nk = order == GF_ORDER_GIVEN ? nb : ((size_t)1 << F->L);
+    const size_t pairs = (size_t)m * F->T;
+    LeafWorkspace W;
+    size_t o = 0;
+    W.bcnt = o; o = al(o + nb * 4);
+    W.bfill = o; o = al(o + nb * 4);
+    W.kcnt = o; o = al(o + nk * 4);
+    W.kfill = o; o = al(o + nk * 4);
+    W.zero_end = o;
+    W.boff = o; o = al(o + (nb + 1) * 4);
+    W.koff = o; o = al(o + (nk + 1) * 4);
+    W.leaf = o; o = al(o + pairs * 4);
+    W.qlist = o; o = al(o + pairs * 4);
+    W.items = o; o = al(o + pairs * 8);
+    W.qhi = o; o = al(o + (size_t)m * F->ldb * 2);
+    W.qlo = o; o = al(o + (size_t)m * F->ldb * 2);
+    W.part = o; o = al(o + pairs * R * 8);
+    W.total = o;
+    return W;
+}
+
+int order_of(int order) { return order == GF_ORDER_GIVEN ? GF_ORDER_GIVEN : GF_ORDER_LOCALITY; }
+
+}  // namespace
+
+const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R,
+                                const QueryExtra &x) {
+    if (precision != GF_BF16_RERANK) return "the leaf-major path runs the bf16 screen only";
+    if (!F->xb || !F->xbn) return "the forest has no bf16 copy";
+    if (x.leaf_budget > 0) return "the leaf-major path runs the one-leaf-per-tree search only";
+    if (x.ncand_out) return "candidate counts are reported by the streaming kernel only";
+    if (R < 1 || R > R_MAX) return "the leaf-major path keeps a shortlist of 1..64";
+    if (k > R) return "k exceeds the shortlist";
+    if ((int64_t)F->T * R > MAX_KEYS) return "T * R above 8192";
+    if (((int64_t)F->T << F->L) > ((int64_t)1 << 22)) return "T * 2^L above 2^22 buckets";
+    if (m * F->T > INT_MAX / 2) return "m * T above 2^30";
+    return nullptr;
+}
+
+// The regrouping pays once leaves are shared: on average at least LEAF_MIN_SHARE queries per leaf.
+constexpr int LEAF_MIN_SHARE = 4;
+
+bool gf_leaf_preferred(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R, const QueryExtra &x) {
+    return gf_leaf_unsupported(F, m, k, precision, R, x) == nullptr && (m >> F->L) >= LEAF_MIN_SHARE;
+}
+
+int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t R, int32_t order) {
+    return (int64_t)leaf_workspace(F, m, std::max(1, std::min(R, R_MAX)), order_of(order)).total;
+}
+
+int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int32_t order,
+                   cudaStream_t st, int64_t *ids, float *dists, void *workspace, int64_t workspace_bytes) {
+    order = order_of(order);
+    const LeafWorkspace W = leaf_workspace(F, m, R, order);
+    char *ws = (char *)workspace;
+    bool own = false;
+    if (ws) {
+        if ((size_t)workspace_bytes < W.total)
+            return gf_fail(GF_EINVAL, "workspace of %lld bytes, %zu needed", (long long)workspace_bytes, W.total);
+    } else {
+        cudaError_t e = cudaMallocAsync((void **)&ws, W.total, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return gf_fail(GF_ENOMEM, "leaf-major workspace of %zu bytes: %s", W.total, cudaGetErrorString(e));
+        }
+        own = true;
+    }
+    auto fail = [&](cudaError_t e, const char *what) {
+        if (own) cudaFreeAsync(ws, st);
+        return gf_cuda_fail(e, what);
+    };
+    int *bcnt = (int *)(ws + W.bcnt), *bfill = (int *)(ws + W.bfill);
+    int *kcnt = (int *)(ws + W.kcnt), *kfill = (int *)(ws + W.kfill);
+    int *boff = (int *)(ws + W.boff), *koff = (int *)(ws + W.koff);
+    int *leaf = (int *)(ws + W.leaf), *qlist = (int *)(ws + W.qlist);
+    int2 *items = (int2 *)(ws + W.items);
+    __nv_bfloat16 *qhi = (__nv_bfloat16 *)(ws + W.qhi), *qlo = (__nv_bfloat16 *)(ws + W.qlo);
+    unsigned long long *part = (unsigned long long *)(ws + W.part);
+    const int nb = F->T << F->L;
+    const int nk = order == GF_ORDER_GIVEN ? nb : (1 << F->L);
+    const long long pairs = (long long)m * F->T;
+    const bool locality = order != GF_ORDER_GIVEN;
+
+    cudaError_t e = cudaMemsetAsync(ws, 0, W.zero_end, st);
+    if (e != cudaSuccess) return fail(e, "workspace memset");
+    int r = gf_descend(F, Q, m, leaf, st);
+    if (r) {
+        if (own) cudaFreeAsync(ws, st);
+        return r;
+    }
+    const unsigned pg = (unsigned)((pairs + 255) / 256), bg = (unsigned)((nb + 255) / 256);
+    k_bucket_count<<<pg, 256, 0, st>>>(leaf, pairs, F->T, F->L, bcnt);
+    k_scan<<<1, 1024, 0, st>>>(bcnt, nb, boff);
+    k_bucket_fill<<<pg, 256, 0, st>>>(leaf, pairs, F->T, F->L, boff, bfill, qlist);
+    k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, locality, kcnt);
+    k_scan<<<1, 1024, 0, st>>>(kcnt, nk, koff);
+    k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, locality, koff, kfill, items);
+    k_qsplit<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldb, qhi, qlo);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major regrouping");
+
+    e = cudaFuncSetAttribute(k_leaf_score, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(k_leaf_score)");
+    LeafArgs A;
+    A.items = items;
+    A.nitems = koff + nk;
+    A.bcnt = bcnt;
+    A.boff = boff;
+    A.qlist = qlist;
+    A.qhi = qhi;
+    A.qlo = qlo;
+    A.part = part;
+    A.R = R;
+    k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_leaf_score launch");
+
+    const size_t msmem = merge_smem(F, R);
+    const unsigned mg = (unsigned)std::min<long long>(m, (long long)F->num_sms * 16);
+    const int ncf = F->ldx / 4 <= 32 ? 1 : F->ldx / 4 <= 64 ? 2 : F->ldx / 4 <= 128 ? 4 : F->ldx / 4 <= 256 ? 8 : 0;
+#define GF_MERGE(NCV)                                                                                    \
+    if (ncf == NCV) {                                                                                    \
+        if (msmem > 48 * 1024 &&                                                                         \
+            (e = cudaFuncSetAttribute(k_leaf_merge<NCV>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                      (int)msmem)) != cudaSuccess)                                       \
+            return fail(e, "cudaFuncSetAttribute(k_leaf_merge)");                                        \
+        k_leaf_merge<NCV><<<mg, 128, msmem, st>>>(view_of(F), Q, m, k, R, part, (long long *)ids, dists); \
+    }
+    GF_MERGE(1) GF_MERGE(2) GF_MERGE(4) GF_MERGE(8) GF_MERGE(0)
+#undef GF_MERGE
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_leaf_merge launch");
+    // a caller's workspace is handed back all zero, as the streaming kernel expects it
+    if (!own && (e = cudaMemsetAsync(ws, 0, W.total, st)) != cudaSuccess) return fail(e, "workspace clear");
+    if (own) cudaFreeAsync(ws, st);
+    return GF_OK;
+}
+
+extern "C" int gf_kernel_status(int32_t *status) {
+    if (!status) return gf_fail(GF_EINVAL, "gf_kernel_status: null pointer");
+    GF_CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    const int zero = 0;
+    GF_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_kernel_status, sizeof v));
+    GF_CUDA_TRY(cudaMemcpyToSymbol(g_kernel_status, &zero, sizeof zero));
+    *status = v;
+    return GF_OK;
+}

@@ -31,7 +31,7 @@ class RandParams(C.Structure):
                 ("householder", C.c_int32)]
 
 
-GF_ALGO_AUTO, GF_ALGO_SORT, GF_ALGO_STREAM = 0, 1, 2
+GF_ALGO_AUTO, GF_ALGO_SORT, GF_ALGO_STREAM, GF_ALGO_LEAF = 0, 1, 2, 3
 GF_ORDER_AUTO, GF_ORDER_GIVEN, GF_ORDER_LOCALITY = 0, 1, 2
 
 
@@ -102,6 +102,7 @@ def lib() -> C.CDLL:
             "gf_server_reset_stats": ([P], i32),
             "gf_server_run_poisson": ([P, P, P, C.c_double, C.c_double, i32, u64, i32, P], i32),
             "gf_server_destroy": ([P], i32),
+            "gf_kernel_status": ([P], i32),
             "gf_last_error": ([], C.c_char_p),
             "gf_version": ([], i32),
             "gf_rand_params_default": ([P], None),
@@ -265,8 +266,8 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
 
 def gf_query_workspace_size(F: Forest, m: int, precision: int = GF_FP32, rerank_R: int = 0,
                             warps_per_cta: int = 0, ctas_per_sm: int = 0, order: int = GF_ORDER_AUTO,
-                            checks: int = 0, eps: float = 0.0) -> int:
-    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, None, GF_ALGO_STREAM, None, None, 0, order,
+                            checks: int = 0, eps: float = 0.0, algo: int = GF_ALGO_STREAM) -> int:
+    o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, None, algo, None, None, 0, order,
               checks, eps)
     b = C.c_int64()
     _check(lib().gf_query_workspace_size(F.handle, m, C.byref(o), C.byref(b)))
@@ -400,6 +401,13 @@ def gf_prio_leaves(F: Forest, Q: torch.Tensor, checks: int, eps: float = 0.0, st
                                 _dptr(leaves, torch.int32, "leaves"), _dptr(nl, torch.int32, "nleaves"),
                                 nb, _stream(stream)))
     return leaves, nl
+
+
+def gf_kernel_status() -> int:
+    """First error code a library kernel recorded since the last call (0: none); synchronizes."""
+    v = C.c_int32(0)
+    _check(lib().gf_kernel_status(C.byref(v)))
+    return v.value
 
 
 def gf_version() -> int:

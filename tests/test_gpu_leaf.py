@@ -1,0 +1,174 @@
+"""The leaf-major batched path (GF_ALGO_LEAF) against the CPU oracle's screened search.
+
+The forest is built by the oracle and imported, so both sides search the same trees.  The oracle's
+bf16 screen ranks the candidate union of every query by the float64 distance to the bf16-rounded
+points, keeps the R best and reranks them exactly; the GPU screen ranks the same union by
+|x~|^2 - 2 x~.q on the tensor cores.  As for the other screened kernels: every reported id must be a
+candidate reported with its float32 distance (1e-5 relative), and a row may differ from the oracle
+only where the two screens order the shortlist boundary differently, which must be rare.  Where
+the shortlist holds every candidate the screen decides nothing, and the answer must equal the
+float32 search bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import screen
+from parity import assert_screened_close, candidate_sets
+
+pytestmark = pytest.mark.gpu
+
+# (name, n, d, m, T, leaf_size, law)
+CASES = [
+    ("tiny", 10_000, 128, 100, 8, 32, "A"),
+    ("ragged", 3001, 37, 57, 5, 9, "B"),          # d not a multiple of 8 or 64; odd n and m
+    ("manytrees", 5000, 64, 40, 40, 16, "A"),     # T above a warp
+    ("long_rows", 3000, 2000, 30, 6, 40, "C"),    # 32 k-steps per row tile
+    ("gist_like", 20_000, 960, 200, 16, 64, "B"),
+    ("shared", 20_000, 96, 3000, 8, 300, "B"),    # ~23 queries per leaf, leaves of 156: two row tiles
+    ("crowded", 8000, 64, 4000, 4, 1000, "A"),    # 500 queries per leaf: 16 chunks; 8 row tiles each
+    ("klein", 10_000, 100, 100, 8, 32, "klein"),
+]
+
+
+@pytest.fixture(scope="module")
+def gf():
+    import paper_1603_09596_gb300 as g
+    g.lib()
+    return g
+
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        _, n, d, m, T, p, law = next(c for c in CASES if c[0] == name)
+        if law == "klein":
+            X, Q = synth.manifold(n, d, m, law, seed=0, qseed=1)
+        else:
+            X, Q = synth.mixture(n, d, m, law, seed=0, qseed=1)
+        F = oracle.build_forest(X, T, p, t=min(5, d), seed=7)
+        _cache[name] = (X, Q, F)
+    return _cache[name]
+
+
+def gpu_forest(gf, X, F):
+    G = gf.gf_forest_import(torch.from_numpy(X).cuda(), F.T, F.leaf_size, F.split_dim, F.split_val, F.perm)
+    gf.gf_forest_add_screen(G, gf.GF_BF16_RERANK)
+    return G
+
+
+def oracle_screen(F, X, Q, k, R):
+    offs, ids = oracle.candidates(F, oracle.descend(F, Q))
+    oi, od, _ = screen.screened_search(F, X, Q, k, R, "bf16", offs, ids)
+    return oi, od, candidate_sets(offs, ids)
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("R", [16, 64])
+def test_leaf_matches_oracle(gf, name, R):
+    X, Q, F = case(name)
+    G = gpu_forest(gf, X, F)
+    k = 10
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.GF_BF16_RERANK, rerank_R=R,
+                         algo=gf.GF_ALGO_LEAF)
+    oi, od, cands = oracle_screen(F, X, Q, k, R)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+    assert gf.gf_kernel_status() == 0
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_leaf_small_k(gf, k):
+    X, Q, F = case("shared")
+    G = gpu_forest(gf, X, F)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.GF_BF16_RERANK, rerank_R=16,
+                         algo=gf.GF_ALGO_LEAF)
+    oi, od, cands = oracle_screen(F, X, Q, k, 16)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+
+
+def test_leaf_full_shortlist_equals_fp32(gf):
+    # at most 64 candidates per query and R = 64: every candidate is reranked, so the answer is
+    # the float32 search's, bit for bit
+    X, Q = synth.mixture(1000, 40, 300, "B", seed=3, qseed=4)
+    F = oracle.build_forest(X, 4, 16, t=5, seed=7)
+    G = gpu_forest(gf, X, F)
+    assert G.info.cand_cap <= 64
+    Qg = torch.from_numpy(Q).cuda()
+    fi, fd = gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_STREAM)
+    li, ld = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=64, algo=gf.GF_ALGO_LEAF)
+    assert torch.equal(fi, li) and torch.equal(fd, ld)
+
+
+def test_leaf_order_changes_no_result(gf):
+    X, Q, F = case("shared")
+    G = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    a = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF,
+                    order=gf.GF_ORDER_GIVEN)
+    b = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF,
+                    order=gf.GF_ORDER_LOCALITY)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_leaf_caller_workspace_is_left_zero(gf):
+    X, Q, F = case("crowded")
+    G = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    nb = gf.gf_query_workspace_size(G, Q.shape[0], precision=gf.GF_BF16_RERANK, rerank_R=16,
+                                    algo=gf.GF_ALGO_LEAF)
+    ws = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    a = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_LEAF, workspace=ws)
+    b = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_LEAF)
+    torch.cuda.synchronize()
+    assert int(ws.count_nonzero()) == 0
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    # the same workspace then serves the streaming kernel, which needs it zero
+    ns = gf.gf_query_workspace_size(G, Q.shape[0], precision=gf.GF_BF16_RERANK, rerank_R=16)
+    ws2 = torch.zeros(max(nb, ns), dtype=torch.uint8, device="cuda")
+    gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_LEAF, workspace=ws2)
+    s = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_STREAM, workspace=ws2)
+    t = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_STREAM)
+    assert torch.equal(s[0], t[0]) and torch.equal(s[1], t[1])
+
+
+def test_leaf_agrees_with_streaming_screen(gf):
+    # two float32 screens of the same candidates: they may order the shortlist boundary
+    # differently, so a few rows can differ; every answer is within the other's tolerance
+    X, Q, F = case("gist_like")
+    G = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    a = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF)
+    b = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_STREAM)
+    same = (a[0] == b[0]).all(dim=1).float().mean().item()
+    assert same >= 0.97
+
+
+def test_leaf_reflected_forest(gf):
+    X, Q, F0 = case("tiny")
+    rng = np.random.default_rng(77)
+    U = rng.standard_normal((F0.T, F0.d))
+    U = (U / np.linalg.norm(U, axis=1, keepdims=True)).astype(np.float32)
+    F = oracle.build_forest(X, F0.T, F0.leaf_size, t=5, seed=7, U=U)
+    G = gpu_forest(gf, X, F)
+    gf.gf_forest_set_reflections(G, U)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, precision=gf.GF_BF16_RERANK, rerank_R=32,
+                         algo=gf.GF_ALGO_LEAF)
+    oi, od, cands = oracle_screen(F, X, Q, 10, 32)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+
+
+def test_leaf_rejects_what_it_does_not_run(gf):
+    X, Q, F = case("tiny")
+    G = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    for kw in (dict(precision=gf.GF_FP32),                                   # float32 scoring
+               dict(precision=gf.GF_BF16_RERANK, rerank_R=65),               # shortlist above 64
+               dict(precision=gf.GF_BF16_RERANK, rerank_R=16, checks=64)):  # priority search
+        with pytest.raises(gf.GFError) as e:
+            gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_LEAF, **kw)
+        assert e.value.code == gf.GF_EUNSUPPORTED
+    assert gf.gf_kernel_status() == 0

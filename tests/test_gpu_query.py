@@ -11,7 +11,7 @@ import torch
 import oracle
 import synth
 from oracle import screen
-from parity import RTOL, assert_topk_close, candidate_sets
+from parity import RTOL, assert_screened_close, assert_topk_close, candidate_sets
 
 pytestmark = pytest.mark.gpu
 
@@ -164,28 +164,6 @@ def test_query_on_side_stream(gf):
 
 
 # ---------------------------------------------------------------- screened precisions
-
-def assert_screened_close(X, Q, gi, gd, oi, od, cands, max_frac=0.03):
-    """Like assert_topk_close, but a row may also differ where the float32 screen and the float64
-    screen order the shortlist boundary differently; every reported id must still be a candidate
-    reported with its exact distance, and such rows must be rare."""
-    m, k = oi.shape
-    bad = 0
-    for i in range(m):
-        fin = oi[i] >= 0
-        assert np.array_equal(gi[i] >= 0, fin)
-        if np.array_equal(gi[i], oi[i]):
-            np.testing.assert_allclose(gd[i][fin], od[i][fin], rtol=RTOL)
-            continue
-        bad += 1
-        for j in np.nonzero(fin)[0]:
-            gid = int(gi[i, j])
-            assert gid in cands[i]
-            true = oracle.dist2(Q[i], X[gid])
-            assert abs(true - gd[i, j]) <= RTOL * max(true, 1e-30)
-        assert np.all(np.diff(gd[i][fin]) >= 0)
-    assert bad <= max(1, int(max_frac * m)), f"{bad} of {m} rows differ"
-
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 @pytest.mark.parametrize("name", ["tiny", "ragged", "long_rows", "gist_like"])
