@@ -71,7 +71,7 @@ typedef struct gf_rand_params {
                             pairs are grouped by the leaf they reach, each leaf's rows are read once
                             per group of up to 32 queries and scored against all of them on the
                             tensor cores; per query the trees' shortlists are merged, de-duplicated
-                            by id and reranked in float32.  R <= 64, T * R <= 8192,
+                            by id and reranked in float32.  R <= 32, T * R <= 8192,
                             T * 2^L <= 2^22; the workspace need not be zero and is left zero */
 
 /* Order in which the streaming kernel's CTAs take the queries of a batch.  Results do not depend

@@ -44,10 +44,9 @@ namespace {
 constexpr int NQ = 32;           // queries per chunk: the MMA's N
 constexpr int BM = 128;          // leaf rows per tile: the MMA's M, one tensor-memory lane each
 constexpr int BK = 64;           // bf16 values per k-step: one 128-byte swizzled row
-constexpr int STAGES = 5;        // shared-memory pipeline depth
-constexpr int LAG = 3;           // stages a producer thread keeps in flight before it signals one
-constexpr int R_MAX = 64;        // longest shortlist per (query, tree)
-constexpr int CAP = 256;         // per-query key buffer of the epilogue
+constexpr int STAGES = 7;        // shared-memory pipeline depth
+constexpr int LAG = 5;           // stages a producer thread keeps in flight before it signals one
+constexpr int R_MAX = 32;        // longest shortlist per (query, tree): one key per lane
 constexpr int A_BYTES = BM * 128;
 constexpr int B_BYTES = NQ * 128;
 constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // leaf rows, query hi, query lo
@@ -60,11 +59,8 @@ static_assert(LAG < STAGES, "a producer must signal a stage before it needs it a
 
 // shared-memory plan of k_leaf_score (offsets from a 1024-aligned base)
 constexpr int SM_STAGES = 0;
-constexpr int SM_BUFQ = SM_STAGES + STAGES * STAGE_BYTES;
-constexpr int SM_TAU = SM_BUFQ + NQ * CAP * 8;
-constexpr int SM_CNT = SM_TAU + NQ * 8;
-constexpr int SM_QID = SM_CNT + NQ * 4;
-constexpr int SM_BAR = SM_QID + NQ * 4;  // full[STAGES] empty[STAGES] dfull[2] dempty[2] fin
+constexpr int SM_WL = SM_STAGES + STAGES * STAGE_BYTES;  // the epilogue warps' lists [4][NQ][32]
+constexpr int SM_BAR = SM_WL + 4 * NQ * 32 * 8;           // full[STAGES] empty[STAGES] dfull[2] dempty[2] fin
 constexpr int SM_MISC = SM_BAR + (2 * STAGES + 5) * 8;  // tensor-memory base, abort flag
 constexpr int SM_TOTAL = SM_MISC + 16;
 constexpr int SMEM_BYTES = SM_TOTAL + 1024;  // slack for aligning the base
@@ -199,29 +195,62 @@ __device__ __forceinline__ uint32_t ord_f32(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// ---------------------------------------------------------------- warp sort of a key buffer
+// ---------------------------------------------------------------- per-warp key lists
+//
+// A list is the ascending sequence of the best keys seen so far, one key per lane: lane i holds
+// entry i of the first RL lanes (RL = the shortlist rounded up to a power of two), KEY_NONE where
+// the list is not full.
 
-// Sort a[0..cnt) ascending (cnt <= CAP) by one warp; positions cnt..P-1 become KEY_NONE.
-__device__ void warp_sort_keys(unsigned long long *a, int cnt) {
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a < b ? b : a; }
+
+// ascending bitonic sort of one key per lane over the warp
+__device__ __forceinline__ unsigned long long warp_sort32(unsigned long long x) {
     const int lane = threadIdx.x & 31;
-    int P = 2;
-    while (P < cnt) P <<= 1;
-    for (int i = cnt + lane; i < P; i += 32) a[i] = KEY_NONE;
-    __syncwarp();
-    for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < (P >> 1); i += 32) {
-                const int lo = 2 * i - (i & (stride - 1));
-                const int hi = lo + stride;
-                const unsigned long long x = a[lo], y = a[hi];
-                if ((x > y) == ((lo & size) == 0)) {
-                    a[lo] = y;
-                    a[hi] = x;
-                }
-            }
-            __syncwarp();
+            const unsigned long long y = __shfl_xor_sync(FULL, x, stride);
+            const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+            x = keep_min ? umin64(x, y) : umax64(x, y);
         }
     }
+    return x;
+}
+
+// The RL smallest keys of two ascending lists a and b, ascending.  min(a_i, b_{RL-1-i}) is the
+// lower half of a bitonic merge: a bitonic sequence holding the RL smallest of a and b; the
+// half-cleaners sort it.
+__device__ __forceinline__ unsigned long long warp_merge_top(unsigned long long a, unsigned long long b, int RL) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long br = __shfl_sync(FULL, b, (RL - 1 - lane) & 31);
+    unsigned long long c = lane < RL ? umin64(a, br) : KEY_NONE;
+    for (int stride = RL >> 1; stride > 0; stride >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(FULL, c, stride);
+        c = (lane & stride) == 0 ? umin64(c, y) : umax64(c, y);
+    }
+    return c;
+}
+
+// Add the keys of the lanes in `bl` (all below the list's R-th key when the ballot was taken) to
+// the list: one by one when they are few, else sorted and merged.
+__device__ __noinline__ unsigned long long list_add(unsigned long long lst, unsigned long long key, unsigned bl, int R,
+                                                    int RL) {
+    const int lane = threadIdx.x & 31;
+    if (__popc(bl) > 4) return warp_merge_top(lst, warp_sort32((bl >> lane) & 1u ? key : KEY_NONE), RL);
+    while (bl) {
+        const int src = __ffs(bl) - 1;
+        bl &= bl - 1;
+        const unsigned long long kk = __shfl_sync(FULL, key, src);
+        if (kk < __shfl_sync(FULL, lst, R - 1)) {
+            const int pos = __popc(__ballot_sync(FULL, lane < RL && lst < kk));
+            const unsigned long long up = __shfl_up_sync(FULL, lst, 1);
+            if (lane < RL && lane > pos) lst = up;
+            if (lane == pos) lst = kk;
+        }
+    }
+    return lst;
 }
 
 // ---------------------------------------------------------------- the scoring kernel
@@ -252,10 +281,7 @@ __device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A,
 __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArgs A) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned long long *bufq = reinterpret_cast<unsigned long long *>(sm + SM_BUFQ);
-    unsigned long long *tau = reinterpret_cast<unsigned long long *>(sm + SM_TAU);
-    int *cnt = reinterpret_cast<int *>(sm + SM_CNT);
-    int *qid_s = reinterpret_cast<int *>(sm + SM_QID);
+    unsigned long long *wl = reinterpret_cast<unsigned long long *>(sm + SM_WL);
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + SM_BAR);
     uint64_t *empty = full + STAGES;
     uint64_t *dfull = empty + STAGES;
@@ -396,21 +422,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue: screened keys, R best per query
+        // Each warp keeps, for every query of the chunk, the list of the R best keys of its own
+        // 32 rows of every tile; the four lists are merged when the chunk is done.
         const int et = tid;  // tile row and tensor-memory lane
+        const int R = A.R;
+        int RL = 1;
+        while (RL < R) RL <<= 1;
         uint32_t tile = 0;
         bool ok = true;
-        for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+        for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
             int t, rows, q0pos, nq;
             long long lo;
             chunk_of(F, A, w, t, lo, rows, q0pos, nq);
-            if (et < NQ) {
-                cnt[et] = 0;
-                tau[et] = KEY_NONE;
-                qid_s[et] = et < nq ? A.qlist[q0pos + et] : -1;
-            }
-            epi_sync();
+            unsigned long long lst[NQ];
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) lst[j] = KEY_NONE;
             const int MT = (rows + BM - 1) / BM;
-            for (int mt = 0; mt < MT; ++mt, ++tile) {
+            for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
                 const int r = mt * BM + et;
                 const bool valid = r < rows;
                 const int id = valid ? __ldg(F.perm + (size_t)t * F.n + lo + r) : 0;
@@ -418,55 +446,37 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                 const uint32_t buf = tile & 1;
                 float v[32];
                 if (!mbar_wait(dfull + buf, (tile >> 1) & 1, abort_flag)) ok = false;
-                if (ok) {
-                    tc_fence_after();
-                    tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * NQ, v);
-                    tc_fence_before();
-                    mbar_arrive(dempty + buf);
-                }
-                if (epi_any(!ok)) {
-                    ok = false;
-                    break;
-                }
+                ok = __all_sync(FULL, ok);
+                if (!ok) break;
+                tc_fence_after();
+                tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * NQ, v);
+                tc_fence_before();
+                mbar_arrive(dempty + buf);
 #pragma unroll
                 for (int j = 0; j < NQ; ++j) {
                     if (j < nq) {
                         const float s = fmaf(-2.f, v[j], xn);
                         const unsigned long long key =
                             valid ? (((unsigned long long)ord_f32(s) << 32) | (unsigned)id) : KEY_NONE;
-                        const bool pass = key < tau[j];
-                        const unsigned bl = __ballot_sync(FULL, pass);
-                        if (bl) {
-                            const int leader = __ffs(bl) - 1;
-                            int base = 0;
-                            if (lane == leader) base = atomicAdd(&cnt[j], __popc(bl));
-                            base = __shfl_sync(FULL, base, leader);
-                            if (pass) bufq[j * CAP + base + __popc(bl & ((1u << lane) - 1u))] = key;
-                        }
+                        const unsigned bl = __ballot_sync(FULL, key < __shfl_sync(FULL, lst[j], R - 1));
+                        if (bl) lst[j] = list_add(lst[j], key, bl, R, RL);
                     }
                 }
-                epi_sync();
-                // keep the R best of any buffer that the next tile could overflow
-                for (int j = warp; j < nq; j += 4) {
-                    if (cnt[j] > CAP - BM) {
-                        warp_sort_keys(bufq + j * CAP, cnt[j]);
-                        if (lane == 0) {
-                            cnt[j] = A.R;
-                            tau[j] = bufq[j * CAP + A.R - 1];
-                        }
-                    }
-                }
-                epi_sync();
             }
-            if (!ok) break;
-            // the chunk is done: each query's R best keys of this tree's leaf
-            for (int j = warp; j < nq; j += 4) {
-                const int c = cnt[j];
-                warp_sort_keys(bufq + j * CAP, c);
-                unsigned long long *out = A.part + ((size_t)qid_s[j] * F.T + t) * A.R;
-                for (int i = lane; i < A.R; i += 32) out[i] = i < c ? bufq[j * CAP + i] : KEY_NONE;
-            }
+            // all four warps are done with the chunk (and with the previous chunk's lists)
+            if (epi_any(!ok)) break;
+#pragma unroll
+            for (int j = 0; j < NQ; ++j)
+                if (j < nq) wl[(warp * NQ + j) * 32 + lane] = lst[j];
             epi_sync();
+            for (int j = warp; j < nq; j += 4) {
+                unsigned long long a = wl[(0 * NQ + j) * 32 + lane], b = wl[(1 * NQ + j) * 32 + lane];
+                unsigned long long c = wl[(2 * NQ + j) * 32 + lane], d = wl[(3 * NQ + j) * 32 + lane];
+                if (lane >= RL) a = b = c = d = KEY_NONE;
+                const unsigned long long best = warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL);
+                const int qid = A.qlist[q0pos + j];
+                if (lane < R) A.part[((size_t)qid * F.T + t) * R + lane] = best;
+            }
         }
     }
     tc_fence_before();
@@ -656,7 +666,7 @@ const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_
     if (!F->xb || !F->xbn) return "the forest has no bf16 copy";
     if (x.leaf_budget > 0) return "the leaf-major path runs the one-leaf-per-tree search only";
     if (x.ncand_out) return "candidate counts are reported by the streaming kernel only";
-    if (R < 1 || R > R_MAX) return "the leaf-major path keeps a shortlist of 1..64";
+    if (R < 1 || R > R_MAX) return "the leaf-major path keeps a shortlist of 1..32";
     if (k > R) return "k exceeds the shortlist";
     if ((int64_t)F->T * R > MAX_KEYS) return "T * R above 8192";
     if (((int64_t)F->T << F->L) > ((int64_t)1 << 22)) return "T * 2^L above 2^22 buckets";

@@ -68,7 +68,7 @@ def oracle_screen(F, X, Q, k, R):
 
 
 @pytest.mark.parametrize("name", [c[0] for c in CASES])
-@pytest.mark.parametrize("R", [16, 64])
+@pytest.mark.parametrize("R", [16, 32])
 def test_leaf_matches_oracle(gf, name, R):
     X, Q, F = case(name)
     G = gpu_forest(gf, X, F)
@@ -91,15 +91,15 @@ def test_leaf_small_k(gf, k):
 
 
 def test_leaf_full_shortlist_equals_fp32(gf):
-    # at most 64 candidates per query and R = 64: every candidate is reranked, so the answer is
+    # at most 32 candidates per query and R = 32: every candidate is reranked, so the answer is
     # the float32 search's, bit for bit
     X, Q = synth.mixture(1000, 40, 300, "B", seed=3, qseed=4)
-    F = oracle.build_forest(X, 4, 16, t=5, seed=7)
+    F = oracle.build_forest(X, 4, 8, t=5, seed=7)
     G = gpu_forest(gf, X, F)
-    assert G.info.cand_cap <= 64
+    assert G.info.cand_cap <= 32
     Qg = torch.from_numpy(Q).cuda()
     fi, fd = gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_STREAM)
-    li, ld = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=64, algo=gf.GF_ALGO_LEAF)
+    li, ld = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF)
     assert torch.equal(fi, li) and torch.equal(fd, ld)
 
 
@@ -166,7 +166,7 @@ def test_leaf_rejects_what_it_does_not_run(gf):
     G = gpu_forest(gf, X, F)
     Qg = torch.from_numpy(Q).cuda()
     for kw in (dict(precision=gf.GF_FP32),                                   # float32 scoring
-               dict(precision=gf.GF_BF16_RERANK, rerank_R=65),               # shortlist above 64
+               dict(precision=gf.GF_BF16_RERANK, rerank_R=33),               # shortlist above 32
                dict(precision=gf.GF_BF16_RERANK, rerank_R=16, checks=64)):  # priority search
         with pytest.raises(gf.GFError) as e:
             gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_LEAF, **kw)
