@@ -8,9 +8,10 @@
 // query.  Here:
 //   1. descend: leaf[q][t] for every (query, tree);
 //   2. bucket the (query, tree) pairs by (tree, leaf) (counting sort);
-//   3. cut every bucket into chunks of at most NQ queries and order the chunks by the smallest
-//      tree-0 leaf among their queries, so chunks of different trees that cover the same region of
-//      the data run at about the same time and find each other's rows in L2;
+//   3. cut every bucket into chunks of at most NQ queries and order the chunks: those of tree 0
+//      first, then the others by the smallest tree-0 leaf among their queries, so chunks of
+//      different trees that cover the same region of the data run at about the same time and find
+//      each other's rows in L2;
 //   4. score (k_leaf_score): one persistent CTA per SM walks the chunks.  A chunk's leaf rows are
 //      staged in shared memory 128 at a time and multiplied against the chunk's queries on the
 //      tensor cores (tcgen05.mma, bf16 inputs, float32 accumulators in tensor memory).  The screened
@@ -18,7 +19,12 @@
 //      |x~ - q|^2 does (the two differ by |q|^2).  x~ is the bf16 copy of the forest; the query
 //      enters as two bf16 parts hi + lo (hi = bf16(q), lo = bf16(q - hi)), i.e. with about 16
 //      significant bits, so the screen is the distance to the bf16 points, as in the other kernels.
-//      Each (query, tree) keeps the R best (score, id) keys of its leaf;
+//      Each (query, tree) keeps the R best (score, id) keys of its leaf that lie below the query's
+//      bound tau_q, an upper bound on the R-th best key of the query's whole candidate union: the
+//      R-th best key of any of its leaves is one.  The chunks of tree 0 run first (a launch of
+//      their own) and set tau_q; every later chunk lowers it with its own R-th best (atomicMin).
+//      Nothing in the union's R best is lost: such a key lies below tau_q and among the R best of
+//      its leaf;
 //   5. merge (k_leaf_merge): per query the T lists are de-duplicated by id, the R best screened
 //      ids are rescored in float32 (direct form, the same code as the other kernels' rerank) and
 //      the k nearest are written in (distance, id) order.
@@ -41,21 +47,23 @@ __device__ int g_kernel_status = 0;  // first error a kernel of the library reco
 
 namespace {
 
-constexpr int NQ = 32;           // queries per chunk: the MMA's N
+constexpr int NQ = 16;           // queries per chunk (the MMA's N is 2 NQ: parts hi and lo)
 constexpr int BM = 128;          // leaf rows per tile: the MMA's M, one tensor-memory lane each
 constexpr int BK = 64;           // bf16 values per k-step: one 128-byte swizzled row
-constexpr int STAGES = 7;        // shared-memory pipeline depth
-constexpr int LAG = 5;           // stages a producer thread keeps in flight before it signals one
+constexpr int STAGES = 10;       // shared-memory pipeline depth
+constexpr int PROD_WARPS = 9;    // producer warps; each loads whole stages, one at a time
 constexpr int R_MAX = 32;        // longest shortlist per (query, tree): one key per lane
 constexpr int A_BYTES = BM * 128;
 constexpr int B_BYTES = NQ * 128;
-constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // leaf rows, query hi, query lo
-constexpr int TMEM_COLS = 2 * NQ;                   // two accumulators of NQ float32 columns
-constexpr int EPI_THREADS = 128, PROD_THREADS = 128;
-constexpr int THREADS = EPI_THREADS + PROD_THREADS + 32;
+constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // leaf rows, then one B tile of MMA_N rows: hi, lo
+constexpr int MMA_N = 2 * NQ;                       // the query parts hi and lo side by side
+constexpr int TMEM_COLS = 2 * MMA_N;                // two accumulators of MMA_N float32 columns
+constexpr int EPI_THREADS = 128;                        // warps 0-3: tensor-memory lane quadrants 0-3
+constexpr int MMA_WARP = 4 + PROD_WARPS;                  // warps 4 .. 3 + PROD_WARPS load
+constexpr int THREADS = (MMA_WARP + 1) * 32;
 constexpr int MAX_KEYS = 8192;                      // T * R limit of the merge
 static_assert(STAGE_BYTES % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
-static_assert(LAG < STAGES, "a producer must signal a stage before it needs it again");
+static_assert(PROD_WARPS <= STAGES, "every producer warp needs a stage of its own");
 
 // shared-memory plan of k_leaf_score (offsets from a 1024-aligned base)
 constexpr int SM_STAGES = 0;
@@ -142,8 +150,9 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16 with bf16 A and B, float32 D, both K-major, M = BM, N = NQ.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NQ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: kind::f16 with bf16 A and B, float32 D, both K-major, M = BM, N = MMA_N.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
@@ -159,21 +168,16 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 32 consecutive float32 columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 16 consecutive float32 columns of this thread's tensor-memory lane (completed by tmem_wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory"); }
 
@@ -257,12 +261,14 @@ __device__ __noinline__ unsigned long long list_add(unsigned long long lst, unsi
 
 struct LeafArgs {
     const int2 *items;     // (bucket, first query of the chunk)
-    const int *nitems;     // device count of items
+    const int *item_lo;    // device: first item of this launch
+    const int *item_hi;    // device: end of this launch's items
     const int *bcnt;       // queries per bucket
     const int *boff;       // first position of each bucket in qlist
     const int *qlist;      // query ids grouped by bucket
     const __nv_bfloat16 *qhi, *qlo;  // [m][ldb] query parts
     unsigned long long *part;        // [m][T][R] screened keys
+    unsigned long long *tau;         // [m] upper bound on each query's R-th best key
     int R;
 };
 
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full + s, PROD_THREADS);
+            mbar_init(full + s, 32);  // the lanes of the stage's producer warp
             mbar_init(empty + s, 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {  // the MMA warp owns the tensor memory
+    if (warp == MMA_WARP) {  // the MMA warp owns the tensor memory
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "n"(TMEM_COLS)
                      : "memory");
@@ -314,78 +320,81 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int nitems = *A.nitems;
+    const int item_lo = *A.item_lo, item_hi = *A.item_hi;
     const int KC = (F.d + BK - 1) / BK;
     const uint32_t stage0 = smem_u32(sm + SM_STAGES);
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 4 && warp < MMA_WARP) {
         // ------------------------------------------------ producers: leaf rows and query parts
-        const int pt = tid - EPI_THREADS;
-        const int c = pt & 7, rsub = pt >> 3;  // 16-byte column chunk, first row
-        uint32_t it = 0;
+        // Stage g of the CTA's stream belongs to producer warp g % PROD_WARPS.  The warp copies
+        // the whole stage (lane: one 16-byte column chunk of every fourth row), waits for its own
+        // copies, makes them visible to the tensor cores and signals the stage full: no stage
+        // waits for another one's copies.
+        const int pw = warp - 4;
+        const int c = lane & 7, r0 = lane >> 3;  // column chunk; rows r0, r0 + 4, ...
+        uint32_t it = 0;                          // stages of the CTA's earlier chunks
         bool ok = true;
-        for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+        for (int w = item_lo + blockIdx.x; w < item_hi && ok; w += gridDim.x) {
             int t, rows, q0pos, nq;
             long long lo;
             chunk_of(F, A, w, t, lo, rows, q0pos, nq);
-            int qid[2];
+            int qid[NQ / 4];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int j = rsub + 16 * i;
+            for (int i = 0; i < NQ / 4; ++i) {
+                const int j = r0 + 4 * i;
                 qid[i] = j < nq ? A.qlist[q0pos + j] : -1;
             }
-            const int MT = (rows + BM - 1) / BM;
-            for (int mt = 0; mt < MT && ok; ++mt) {
-                int id[8];
+            const int nst = (rows + BM - 1) / BM * KC;
+            int ids[BM / 4];  // point ids of the lane's rows of tile `cur`
+            int cur = -1;
+            for (int st = (int)((pw + PROD_WARPS - it % PROD_WARPS) % PROD_WARPS); st < nst; st += PROD_WARPS) {
+                const uint32_t g = it + st;
+                const uint32_t s = g % STAGES;
+                const int mt = st / KC, kc = st - mt * KC;
+                if (mt != cur) {
+                    cur = mt;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int r = mt * BM + rsub + 16 * i;
-                    id[i] = r < rows ? __ldg(F.perm + (size_t)t * F.n + lo + r) : -1;
+                    for (int i = 0; i < BM / 4; ++i) {
+                        const int gr = mt * BM + r0 + 4 * i;
+                        ids[i] = gr < rows ? __ldg(F.perm + (size_t)t * F.n + lo + gr) : -1;
+                    }
                 }
-                for (int kc = 0; kc < KC; ++kc) {
-                    const uint32_t s = it % STAGES;
-                    if (!mbar_wait(empty + s, ((it / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    const int col = kc * BK + c * 8;
-                    const int nb = max(0, min(16, (F.d - col) * 2));
-                    const uint32_t sa = stage0 + s * STAGE_BYTES;
+                if (!mbar_wait(empty + s, ((g / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                const int col = kc * BK + c * 8;
+                const int nb = max(0, min(16, (F.d - col) * 2));
+                const uint32_t sa = stage0 + s * STAGE_BYTES;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int r = rsub + 16 * i;
-                        const bool live = id[i] >= 0 && nb > 0;
-                        const __nv_bfloat16 *src = live ? F.xb + (size_t)id[i] * F.ldb + col : F.xb;
-                        cp_async16(sa + r * 128 + ((c ^ (r & 7)) << 4), src, live ? nb : 0);
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const __nv_bfloat16 *qb = h ? A.qlo : A.qhi;
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) {
-                            const int j = rsub + 16 * i;
-                            const bool live = qid[i] >= 0 && nb > 0;
-                            const __nv_bfloat16 *src = live ? qb + (size_t)qid[i] * F.ldb + col : qb;
-                            cp_async16(sa + A_BYTES + h * B_BYTES + j * 128 + ((c ^ (j & 7)) << 4), src, live ? nb : 0);
-                        }
-                    }
-                    cp_async_commit();
-                    if (it >= LAG) {
-                        cp_async_wait<LAG>();
-                        fence_proxy_async();
-                        mbar_arrive(full + (it - LAG) % STAGES);
-                    }
-                    ++it;
+                for (int i = 0; i < BM / 4; ++i) {
+                    const int r = r0 + 4 * i;
+                    const bool live = ids[i] >= 0 && nb > 0;
+                    const __nv_bfloat16 *src = live ? F.xb + (size_t)ids[i] * F.ldb + col : F.xb;
+                    cp_async16(sa + r * 128 + ((c ^ (r & 7)) << 4), src, live ? nb : 0);
                 }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const __nv_bfloat16 *qb = h ? A.qlo : A.qhi;
+#pragma unroll
+                    for (int i = 0; i < NQ / 4; ++i) {
+                        const int j = r0 + 4 * i;
+                        const bool live = qid[i] >= 0 && nb > 0;
+                        const __nv_bfloat16 *src = live ? qb + (size_t)qid[i] * F.ldb + col : qb;
+                        cp_async16(sa + A_BYTES + h * B_BYTES + j * 128 + ((c ^ (j & 7)) << 4), src, live ? nb : 0);
+                    }
+                }
+                cp_async_commit();
+                cp_async_wait<0>();
+                fence_proxy_async();
+                mbar_arrive(full + s);
             }
+            it += nst;
         }
         cp_async_wait<0>();
-        fence_proxy_async();
-        if (ok)
-            for (uint32_t j = it >= LAG ? it - LAG : 0; j < it; ++j) mbar_arrive(full + j % STAGES);
-    } else if (warp == 8) {
+    } else if (warp == MMA_WARP) {
         // ------------------------------------------------ MMA issue (one thread)
         if (lane == 0) {
             uint32_t it = 0, tile = 0;
             bool ok = true;
-            for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+            for (int w = item_lo + blockIdx.x; w < item_hi && ok; w += gridDim.x) {
                 int t, rows, q0pos, nq;
                 long long lo;
                 chunk_of(F, A, w, t, lo, rows, q0pos, nq);
@@ -394,20 +403,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                     const uint32_t buf = tile & 1;
                     if (!mbar_wait(dempty + buf, ((tile >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + buf * NQ;
+                    const uint32_t d_tmem = tmem_base + buf * MMA_N;
                     for (int kc = 0; kc < KC; ++kc, ++it) {
                         const uint32_t s = it % STAGES;
                         if (!mbar_wait(full + s, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = stage0 + s * STAGE_BYTES;
                         const uint64_t da = sdesc_sw128(sa);
-                        const uint64_t dh = sdesc_sw128(sa + A_BYTES);
-                        const uint64_t dl = sdesc_sw128(sa + A_BYTES + B_BYTES);
+                        const uint64_t db = sdesc_sw128(sa + A_BYTES);  // rows 0..NQ-1 hi, NQ.. lo
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk) {  // 16 bf16 (32 bytes) per instruction
-                            mma_bf16(d_tmem, da + 2 * kk, dh + 2 * kk, (kc | kk) != 0);
-                            mma_bf16(d_tmem, da + 2 * kk, dl + 2 * kk, 1u);
-                        }
+                        for (int kk = 0; kk < BK / 16; ++kk)  // 16 bf16 (32 bytes) per instruction
+                            mma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, (kc | kk) != 0);
                         mma_commit(empty + s);
                     }
                     if (!ok) break;
@@ -430,13 +436,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
         while (RL < R) RL <<= 1;
         uint32_t tile = 0;
         bool ok = true;
-        for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        for (int w = item_lo + blockIdx.x; w < item_hi; w += gridDim.x) {
             int t, rows, q0pos, nq;
             long long lo;
             chunk_of(F, A, w, t, lo, rows, q0pos, nq);
             unsigned long long lst[NQ];
 #pragma unroll
             for (int j = 0; j < NQ; ++j) lst[j] = KEY_NONE;
+            // lane j: query j of the chunk and its bound
+            const int my_qid = lane < nq ? A.qlist[q0pos + lane] : 0;
+            const unsigned long long my_tau = lane < nq ? __ldcg(A.tau + my_qid) : KEY_NONE;
             const int MT = (rows + BM - 1) / BM;
             for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
                 const int r = mt * BM + et;
@@ -444,12 +453,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                 const int id = valid ? __ldg(F.perm + (size_t)t * F.n + lo + r) : 0;
                 const float xn = valid ? __ldg(F.xbn + id) : 0.f;
                 const uint32_t buf = tile & 1;
-                float v[32];
                 if (!mbar_wait(dfull + buf, (tile >> 1) & 1, abort_flag)) ok = false;
                 ok = __all_sync(FULL, ok);
                 if (!ok) break;
                 tc_fence_after();
-                tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * NQ, v);
+                const uint32_t ta = tmem_base + ((uint32_t)(warp * 32) << 16) + buf * MMA_N;
+                float v[NQ];  // x~ . (q_hi + q_lo) of the lane's row for every query of the chunk
+#pragma unroll
+                for (int h = 0; h < NQ / 16; ++h) {
+                    uint32_t hi[16], lo16[16];
+                    tmem_ld16(ta + 16 * h, hi);
+                    tmem_ld16(ta + NQ + 16 * h, lo16);
+                    tmem_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[16 * h + i] = __uint_as_float(hi[i]) + __uint_as_float(lo16[i]);
+                }
                 tc_fence_before();
                 mbar_arrive(dempty + buf);
 #pragma unroll
@@ -458,7 +476,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                         const float s = fmaf(-2.f, v[j], xn);
                         const unsigned long long key =
                             valid ? (((unsigned long long)ord_f32(s) << 32) | (unsigned)id) : KEY_NONE;
-                        const unsigned bl = __ballot_sync(FULL, key < __shfl_sync(FULL, lst[j], R - 1));
+                        const unsigned long long thr =
+                            umin64(__shfl_sync(FULL, lst[j], R - 1), __shfl_sync(FULL, my_tau, j));
+                        const unsigned bl = __ballot_sync(FULL, key < thr);
                         if (bl) lst[j] = list_add(lst[j], key, bl, R, RL);
                     }
                 }
@@ -476,13 +496,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                 const unsigned long long best = warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL);
                 const int qid = A.qlist[q0pos + j];
                 if (lane < R) A.part[((size_t)qid * F.T + t) * R + lane] = best;
+                const unsigned long long kth = __shfl_sync(FULL, best, R - 1);
+                if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + qid, kth);
             }
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8)
+    if (warp == MMA_WARP)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(TMEM_COLS)
                      : "memory");
 }
@@ -505,30 +527,31 @@ __global__ void k_bucket_fill(const int *__restrict__ leaf, long long pairs, int
     qlist[boff[u] + atomicAdd(bfill + u, 1)] = (int)(g / T);
 }
 
-// Order key of a bucket: the smallest tree-0 leaf among its queries (locality), or the bucket
-// itself (tree-major order).
+// Order key of a bucket (tree t = u >> L): in locality order 2^L * (t > 0) + the smallest tree-0
+// leaf among its queries, in tree-major order the bucket itself.  Either way the buckets of tree 0
+// take the keys below 2^L.
 __device__ __forceinline__ int bucket_key(int u, const int *bcnt, const int *boff, const int *qlist,
-                                          const int *leaf, int T, bool locality) {
+                                          const int *leaf, int T, int L, bool locality) {
     if (!locality) return u;
     int key = INT_MAX;
     for (int i = 0; i < bcnt[u]; ++i) key = min(key, leaf[(size_t)qlist[boff[u] + i] * T]);
-    return key;
+    return ((u >> L) > 0 ? (1 << L) : 0) + key;
 }
 
 __global__ void k_item_count(int nb, const int *__restrict__ bcnt, const int *__restrict__ boff,
-                             const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int locality,
+                             const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int L, int locality,
                              int *kcnt) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nb || bcnt[u] == 0) return;
-    atomicAdd(kcnt + bucket_key(u, bcnt, boff, qlist, leaf, T, locality), (bcnt[u] + NQ - 1) / NQ);
+    atomicAdd(kcnt + bucket_key(u, bcnt, boff, qlist, leaf, T, L, locality), (bcnt[u] + NQ - 1) / NQ);
 }
 
 __global__ void k_item_fill(int nb, const int *__restrict__ bcnt, const int *__restrict__ boff,
-                            const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int locality,
+                            const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int L, int locality,
                             const int *__restrict__ koff, int *kfill, int2 *items) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nb || bcnt[u] == 0) return;
-    const int key = bucket_key(u, bcnt, boff, qlist, leaf, T, locality);
+    const int key = bucket_key(u, bcnt, boff, qlist, leaf, T, L, locality);
     const int n_it = (bcnt[u] + NQ - 1) / NQ;
     const int base = koff[key] + atomicAdd(kfill + key, n_it);
     for (int i = 0; i < n_it; ++i) items[base + i] = make_int2(u, i * NQ);
@@ -629,13 +652,13 @@ size_t merge_smem(const gf_forest *F, int R) {
 
 struct LeafWorkspace {
     size_t bcnt, bfill, kcnt, kfill, zero_end;  // counters, zeroed by every call
-    size_t boff, koff, leaf, qlist, items, qhi, qlo, part, total;
+    size_t boff, koff, leaf, qlist, items, qhi, qlo, part, tau, total;
 };
 
 LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int R, int order) {
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t nb = (size_t)F->T << F->L;
-    const size_t nk = order == GF_ORDER_GIVEN ? nb : ((size_t)1 << F->L);
+    const size_t nk = order == GF_ORDER_GIVEN ? nb : ((size_t)2 << F->L);
     const size_t pairs = (size_t)m * F->T;
     LeafWorkspace W;
     size_t o = 0;
@@ -652,6 +675,7 @@ LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int R, int order) {
     W.qhi = o; o = al(o + (size_t)m * F->ldb * 2);
     W.qlo = o; o = al(o + (size_t)m * F->ldb * 2);
     W.part = o; o = al(o + pairs * R * 8);
+    W.tau = o; o = al(o + (size_t)m * 8);
     W.total = o;
     return W;
 }
@@ -713,12 +737,14 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     int2 *items = (int2 *)(ws + W.items);
     __nv_bfloat16 *qhi = (__nv_bfloat16 *)(ws + W.qhi), *qlo = (__nv_bfloat16 *)(ws + W.qlo);
     unsigned long long *part = (unsigned long long *)(ws + W.part);
+    unsigned long long *tau = (unsigned long long *)(ws + W.tau);
     const int nb = F->T << F->L;
-    const int nk = order == GF_ORDER_GIVEN ? nb : (1 << F->L);
+    const int nk = order == GF_ORDER_GIVEN ? nb : (2 << F->L);
     const long long pairs = (long long)m * F->T;
     const bool locality = order != GF_ORDER_GIVEN;
 
     cudaError_t e = cudaMemsetAsync(ws, 0, W.zero_end, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tau, 0xff, (size_t)m * 8, st);  // KEY_NONE: no bound yet
     if (e != cudaSuccess) return fail(e, "workspace memset");
     int r = gf_descend(F, Q, m, leaf, st);
     if (r) {
@@ -729,9 +755,9 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     k_bucket_count<<<pg, 256, 0, st>>>(leaf, pairs, F->T, F->L, bcnt);
     k_scan<<<1, 1024, 0, st>>>(bcnt, nb, boff);
     k_bucket_fill<<<pg, 256, 0, st>>>(leaf, pairs, F->T, F->L, boff, bfill, qlist);
-    k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, locality, kcnt);
+    k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, F->L, locality, kcnt);
     k_scan<<<1, 1024, 0, st>>>(kcnt, nk, koff);
-    k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, locality, koff, kfill, items);
+    k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, F->L, locality, koff, kfill, items);
     k_qsplit<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldb, qhi, qlo);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major regrouping");
 
@@ -739,14 +765,20 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(k_leaf_score)");
     LeafArgs A;
     A.items = items;
-    A.nitems = koff + nk;
     A.bcnt = bcnt;
     A.boff = boff;
     A.qlist = qlist;
     A.qhi = qhi;
     A.qlo = qlo;
     A.part = part;
+    A.tau = tau;
     A.R = R;
+    // the chunks of tree 0 (keys below 2^L) set every query's bound; then all the others
+    A.item_lo = koff;
+    A.item_hi = koff + (1 << F->L);
+    k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
+    A.item_lo = koff + (1 << F->L);
+    A.item_hi = koff + nk;
     k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_leaf_score launch");
 

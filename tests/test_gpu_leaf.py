@@ -28,7 +28,7 @@ CASES = [
     ("long_rows", 3000, 2000, 30, 6, 40, "C"),    # 32 k-steps per row tile
     ("gist_like", 20_000, 960, 200, 16, 64, "B"),
     ("shared", 20_000, 96, 3000, 8, 300, "B"),    # ~23 queries per leaf, leaves of 156: two row tiles
-    ("crowded", 8000, 64, 4000, 4, 1000, "A"),    # 500 queries per leaf: 16 chunks; 8 row tiles each
+    ("crowded", 8000, 64, 4000, 4, 1000, "A"),    # 500 queries per leaf: many chunks; 8 row tiles each
     ("klein", 10_000, 100, 100, 8, 32, "klein"),
 ]
 
