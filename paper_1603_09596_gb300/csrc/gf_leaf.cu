@@ -105,8 +105,7 @@ constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after about two 
 
 // Wait for the phase of `parity` to complete.  Returns false (and raises the CTA's abort flag and
 // the device status) if it did not within WAIT_NS, or if another role of the CTA aborted.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_test(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     const uint64_t t0 = globaltimer();
     for (uint32_t spin = 1;; ++spin) {
         if (mbar_test(bar, parity)) return true;
@@ -120,6 +119,10 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
             __nanosleep(64);
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abort_flag);
 }
 
 // 16-byte global -> shared copy that reads `bytes` (0..16) bytes and zero-fills the rest
@@ -154,11 +157,17 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+// The four MMAs of one stage (K = 64 as four steps of 16): D (+)= A B^T, accumulating from the
+// first unless `accumulate` is 0.  Descriptors advance 32 bytes (2 in units of 16) per step.
+__device__ __forceinline__ void mma_stage(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        "{\n .reg .pred p, q;\n setp.ne.b32 p, %3, 0;\n setp.eq.b32 q, 0, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %4, q;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %4, q;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %4, q;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(accumulate), "r"(IDESC), "l"(a + 2), "l"(b + 2), "l"(a + 4), "l"(b + 4), "l"(a + 6),
+        "l"(b + 6)
         : "memory");
 }
 
@@ -392,8 +401,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------ MMA issue (one thread)
         if (lane == 0) {
-            uint32_t it = 0, tile = 0;
+            uint32_t tile = 0, s = 0, ph = 0;  // next stage slot and the parity of its fill
             bool ok = true;
+            const uint64_t da0 = sdesc_sw128(stage0);            // stage 0's leaf rows
+            const uint64_t db0 = sdesc_sw128(stage0 + A_BYTES);  // stage 0's query rows: hi, then lo
             for (int w = item_lo + blockIdx.x; w < item_hi && ok; w += gridDim.x) {
                 int t, rows, q0pos, nq;
                 long long lo;
@@ -402,19 +413,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                 for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
                     const uint32_t buf = tile & 1;
                     if (!mbar_wait(dempty + buf, ((tile >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    tc_fence_after();
+                    tc_fence_after();  // the epilogue's reads of this accumulator are done
                     const uint32_t d_tmem = tmem_base + buf * MMA_N;
-                    for (int kc = 0; kc < KC; ++kc, ++it) {
-                        const uint32_t s = it % STAGES;
-                        if (!mbar_wait(full + s, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t sa = stage0 + s * STAGE_BYTES;
-                        const uint64_t da = sdesc_sw128(sa);
-                        const uint64_t db = sdesc_sw128(sa + A_BYTES);  // rows 0..NQ-1 hi, NQ.. lo
-#pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk)  // 16 bf16 (32 bytes) per instruction
-                            mma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, (kc | kk) != 0);
+                    for (int kc = 0; kc < KC; ++kc) {
+                        if (!mbar_wait(full + s, ph, abort_flag)) { ok = false; break; }
+                        const uint64_t off = (uint64_t)((s * STAGE_BYTES) >> 4);
+                        mma_stage(d_tmem, da0 + off, db0 + off, kc != 0);
                         mma_commit(empty + s);
+                        if (++s == STAGES) { s = 0; ph ^= 1; }
                     }
                     if (!ok) break;
                     mma_commit(dfull + buf);
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
             // every issued operation has completed before the tensor memory is freed
             mma_commit(fin);
             volatile int no_abort = 0;
-            mbar_wait(fin, 0, &no_abort);
+            mbar_wait_slow(fin, 0, &no_abort);
         }
         __syncwarp();
     } else {
