@@ -38,26 +38,31 @@ HEADLINE = dict(T=32, leaf_size=1024)   # recall@1 >= 0.9 (one leaf per tree)
 SPEC = dict(T=32, leaf_size=64)         # the tree parameters quoted with the workload
 
 
-KERNEL_SOURCES = ["paper_1603_09596_gb300/csrc/gf_query.cu", "paper_1603_09596_gb300/csrc/gf_internal.cuh",
-                  "paper_1603_09596_gb300/csrc/gf_device.cuh", "include/gf.h"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_query_stream_traffic.json")
+# the query kernels' sources and the committed ncu traffic record of each headline algorithm
+_COMMON = ["paper_1603_09596_gb300/csrc/gf_internal.cuh", "paper_1603_09596_gb300/csrc/gf_device.cuh",
+           "paper_1603_09596_gb300/csrc/gf_score.cuh", "include/gf.h"]
+KERNEL_SOURCES = {"stream": ["paper_1603_09596_gb300/csrc/gf_query.cu"] + _COMMON,
+                  "leaf": ["paper_1603_09596_gb300/csrc/gf_leaf.cu"] + _COMMON}
+TRAFFIC_FILES = {"stream": os.path.join(ROOT, "profiles", "k_query_stream_traffic.json"),
+                 "leaf": os.path.join(ROOT, "profiles", "k_leaf_score_traffic.json")}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(algo: str = "leaf") -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[algo]:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the headline launch from the committed ncu record, or None when the
+def recorded_traffic(algo: str):
+    """DRAM bytes per step of the headline algorithm from the committed ncu record, or None when the
     kernel sources changed since the counters were taken."""
-    if not os.path.exists(TRAFFIC_FILE):
+    f = TRAFFIC_FILES[algo]
+    if not os.path.exists(f):
         return None
-    j = json.load(open(TRAFFIC_FILE))
-    if j.get("source_sha256") != kernel_source_hash():
+    j = json.load(open(f))
+    if j.get("source_sha256") != kernel_source_hash(algo):
         return None
     return j
 
@@ -165,19 +170,20 @@ def recall(torch, Xg, Qs, ids, exact_i, exact_d):
     return r1, float(hits.mean())
 
 
-def time_batch(gf, F, Qg, k, prec, steps, warmup, dev, world=1, local=0, no_graph=False, checks=0):
+def time_batch(gf, F, Qg, k, prec, steps, warmup, dev, world=1, local=0, no_graph=False, checks=0, algo=0, R=0):
     """Time `steps` launches of the batch Qg; the launch is captured once in a CUDA graph (with a
     caller workspace, so nothing allocates inside the capture) and replayed per step."""
     import torch
     m = Qg.shape[0]
     ids = torch.empty((m, k), dtype=torch.int64, device=dev)
     dd = torch.empty((m, k), dtype=torch.float32, device=dev)
-    ws = torch.zeros(gf.gf_query_workspace_size(F, m, precision=prec, checks=checks) // 4 + 1, dtype=torch.int32,
-                     device=dev)
+    ws = torch.zeros(gf.gf_query_workspace_size(F, m, precision=prec, rerank_R=R, checks=checks, algo=algo) // 4 + 1,
+                     dtype=torch.int32, device=dev)
     s = torch.cuda.Stream(device=dev)
 
     def launch():
-        gf.gf_query(F, Qg, k, precision=prec, out=(ids, dd), workspace=ws, stream=s, checks=checks)
+        gf.gf_query(F, Qg, k, precision=prec, rerank_R=R, out=(ids, dd), workspace=ws, stream=s, checks=checks,
+                    algo=algo)
 
     with torch.cuda.stream(s):
         for _ in range(warmup):
@@ -221,6 +227,27 @@ def query_bytes(gf, F, prec, C, R, d, k, leaves=0):
     rows = C * (d * b + (4 if prec == gf.GF_FP8_RERANK else 0))
     rerank = R * d * 4 if prec != gf.GF_FP32 else 0
     return rows + rerank + d * 4 + positions * 4 + 12 * k
+
+
+def leaf_bytes(gf, F, Qg, R, k):
+    """Algorithmic bytes of one leaf-major batch: every chunk (a (tree, leaf) bucket cut into groups
+    of at most 16 queries) reads its leaf's bf16 rows with their ids and |x~|^2 once; plus the query
+    (read, split into bf16 parts), the (query, tree) shortlists written and merged, the float32
+    rerank rows and the results.  The query parts re-read per row tile come from L2 (a few tens of
+    MB in all) and are not counted."""
+    import torch
+    inf = F.info
+    m, T, L = Qg.shape[0], inf.T, inf.L
+    leaf = gf.gf_descend(F, Qg).long()
+    u = (leaf + (torch.arange(T, device=Qg.device) << L)).flatten()
+    cnt = torch.bincount(u, minlength=T << L)
+    chunks = (cnt + 15) // 16
+    b = torch.arange(T << L, device=Qg.device) & ((1 << L) - 1)
+    rows = ((b + 1) * inf.n >> L) - (b * inf.n >> L)
+    ldb, ldx = (inf.d + 7) // 8 * 8, (inf.d + 3) // 4 * 4
+    row_bytes = int((chunks * rows).sum()) * (ldb * 2 + 8)
+    other = m * inf.d * 4 * 2 + m * ldb * 2 * 2 + m * T * R * 8 * 2 + m * R * ldx * 4 + m * k * 12
+    return row_bytes + other, int(chunks.sum())
 
 
 def ours(args):
@@ -273,20 +300,38 @@ def ours(args):
         C = float(nc.double().mean())
         entry["cand_per_query"] = round(C, 1)
         leaves = gf.leaf_budget(F, checks) if checks else 0
-        for name, prec in (("fp32", gf.GF_FP32), ("bf16", gf.GF_BF16_RERANK)):
-            tr = autotune.tune(F, Qg[:tune_sample], k, prec, checks=checks)
+        runs = [("fp32", gf.GF_FP32, gf.GF_ALGO_STREAM), ("bf16_stream", gf.GF_BF16_RERANK, gf.GF_ALGO_STREAM)]
+        if not checks:  # the leaf-major path runs the one-leaf-per-tree search
+            runs.append(("bf16_leaf", gf.GF_BF16_RERANK, gf.GF_ALGO_LEAF))
+        tuned = {}
+        for name, prec, algo in runs:
+            if prec not in tuned:
+                tuned[prec] = autotune.tune(F, Qg[:tune_sample], k, prec, checks=checks)
+            tr = tuned[prec]
+            R = tr.get("R", 0)
+            if algo == gf.GF_ALGO_LEAF and R > 32:  # the leaf-major path keeps at most 32
+                continue
             ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, world, local,
-                                         args.no_graph, checks)
+                                         args.no_graph, checks, algo=algo, R=R)
             r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
             mean_ms = statistics.mean(ms)
-            R = tr.get("R", 0)
-            bpq = bytes_per_query(F, prec, C, R, leaves)
+            if algo == gf.GF_ALGO_LEAF:
+                lb, nchunks = leaf_bytes(gf, F, Qg, R, k)
+                bpq = lb / m
+            else:
+                bpq, nchunks = bytes_per_query(F, prec, C, R, leaves), None
             entry[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4),
                            "ms_min": round(min(ms), 4), "recall_at_1": r1, "recall_at_10": rk, "clocks": ck,
-                           "R": R, "warps_per_cta": tr["warps"], "ctas_per_sm": tr["ctas_per_sm"],
-                           "rows_in_flight": tr["rows_in_flight"],
+                           "R": R, "algo": {gf.GF_ALGO_STREAM: "stream", gf.GF_ALGO_LEAF: "leaf"}[algo],
                            "bytes_per_query": round(bpq),
                            "achieved_gbs": round(bpq * m / (mean_ms / 1e3) / 1e9, 1)}
+            if algo == gf.GF_ALGO_LEAF:
+                entry[name]["chunks"] = nchunks
+            else:
+                entry[name].update(warps_per_cta=tr["warps"], ctas_per_sm=tr["ctas_per_sm"],
+                                   rows_in_flight=tr["rows_in_flight"])
+        bf = [entry[nm] for nm in ("bf16_stream", "bf16_leaf") if nm in entry]
+        entry["bf16"] = max(bf, key=lambda e: e["qps"])
         return F, entry
 
     Fh, head = run_forest(HEADLINE["T"], HEADLINE["leaf_size"], args.tune_sample)
@@ -307,16 +352,20 @@ def ours(args):
     Fc, cc = (Fh, 0) if point_id.startswith("one_leaf") else (Fs, args.prio_checks)
     value, mean_ms = aggregate(best["ms_per_step"], m, world, device=dev)
     achieved = best["bytes_per_query"] * m / (mean_ms / 1e3) / 1e9
-    tr = recorded_traffic()
+    algo = best["algo"]
+    tr = recorded_traffic(algo)
     if tr and tr.get("point") != point_id:
         tr = None
+    kernel = ("k_leaf_score (2 launches: tree 0, then the rest; tcgen05 bf16 screen) dominant, with the "
+              "regrouping kernels and k_leaf_merge (dedupe + fp32 rerank + top-k); bytes and time of the whole step"
+              if algo == "leaf" else
+              "k_query_stream<bf16> (leaves + bitmap dedupe + bf16 screen + fp32 rerank + top-k), "
+              + ("k_prio_leaves + " if "priority" in point_id else "") + "1 query launch/step")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "traffic": tr["bytes_per_launch"] if tr else None,
             "traffic_note": tr["note"] if tr else "no ncu record for the current kernel sources",
             "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
-            "kernel": "k_query_stream<bf16> (leaves + bitmap dedupe + bf16 screen + fp32 rerank + top-k), "
-                      + ("k_prio_leaves + " if "priority" in point_id else "") + "1 query launch/step",
-            "bytes_per_query": best["bytes_per_query"]}
+            "kernel": kernel, "bytes_per_query": best["bytes_per_query"]}
 
     # end to end through the public API with host buffers
     Qh = torch.from_numpy(Q).pin_memory()
@@ -346,12 +395,13 @@ def ours(args):
            "d2h_bytes_per_step": m * k * 12}
 
     # latency under load: single-query requests to the headline forest, Poisson arrivals at half
-    # the measured batch throughput, continuous batching (up to 1024 per batch, 4 slots)
+    # the batch throughput of the kernel the server runs (its batches of at most 1024 queries go
+    # through the streaming kernel), continuous batching (4 slots)
     lat = None
     if not args.no_serve:
         srv = gf.Server([Fc], max_batch=1024, slots=4, hbm_budget_bytes=8 << 30, k_max=k,
                         precision=gf.GF_BF16_RERANK, rerank_R=best["R"], checks=cc)
-        rate = 0.5 * value / world
+        rate = 0.5 * chosen["bf16_stream"]["qps"]
         srv.run_poisson([Q[:4096]], rate_qps=min(rate, 5000), duration_s=0.3, k=k, seed=3)
         st = srv.run_poisson([Q], rate_qps=rate, duration_s=args.serve_seconds, k=k, seed=4)
         lat = {"offered_qps": round(rate, 1), "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
@@ -377,7 +427,10 @@ def ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        # library kernels per step: leaf-major = descend, 6 regrouping kernels, query split, 2 scoring
+        # launches, merge; streaming = the 2 locality-order kernels and the query kernel (+ the
+        # priority-queue kernel for the priority point)
+        "gpu_launches": args.steps * (11 if algo == "leaf" else 3 + (1 if "priority" in point_id else 0)),
         "clocks": best["clocks"],
         "fp32_plain": chosen["fp32"],
         "bf16_screen": chosen["bf16"],
@@ -673,7 +726,7 @@ def main():
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB for batch slots")
     args = ap.parse_args()
     if args.source_hash:
-        print(kernel_source_hash())
+        print(json.dumps({a: kernel_source_hash(a) for a in KERNEL_SOURCES}))
     elif args.profile:
         profile(args)
     elif args.serve:
