@@ -49,21 +49,23 @@ namespace {
 
 constexpr int NQ = 16;           // queries per chunk (the MMA's N is 2 NQ: parts hi and lo)
 constexpr int BM = 128;          // leaf rows per tile: the MMA's M, one tensor-memory lane each
-constexpr int BK = 64;           // bf16 values per k-step: one 128-byte swizzled row
-constexpr int STAGES = 10;       // shared-memory pipeline depth
-constexpr int PROD_WARPS = 9;    // producer warps; each loads whole stages, one at a time
+constexpr int BK = 64;           // bf16 values per sub-tile: one 128-byte swizzled row
+constexpr int SUB = 2;           // sub-tiles per pipeline stage: one wait and one release per SUB k-steps
+constexpr int STAGES = 5;        // shared-memory pipeline depth
+constexpr int PROD_WARPS = 10;   // producer warps; each loads whole sub-tiles, one at a time
 constexpr int R_MAX = 32;        // longest shortlist per (query, tree): one key per lane
 constexpr int A_BYTES = BM * 128;
 constexpr int B_BYTES = NQ * 128;
-constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;  // leaf rows, then one B tile of MMA_N rows: hi, lo
+constexpr int SUBTILE_BYTES = A_BYTES + 2 * B_BYTES;  // leaf rows, then one B tile of MMA_N rows: hi, lo
+constexpr int STAGE_BYTES = SUB * SUBTILE_BYTES;
 constexpr int MMA_N = 2 * NQ;                       // the query parts hi and lo side by side
 constexpr int TMEM_COLS = 2 * MMA_N;                // two accumulators of MMA_N float32 columns
 constexpr int EPI_THREADS = 128;                        // warps 0-3: tensor-memory lane quadrants 0-3
 constexpr int MMA_WARP = 4 + PROD_WARPS;                  // warps 4 .. 3 + PROD_WARPS load
 constexpr int THREADS = (MMA_WARP + 1) * 32;
 constexpr int MAX_KEYS = 8192;                      // T * R limit of the merge
-static_assert(STAGE_BYTES % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
-static_assert(PROD_WARPS <= STAGES, "every producer warp needs a stage of its own");
+static_assert(SUBTILE_BYTES % 1024 == 0, "sub-tiles must keep the 1024-byte swizzle alignment");
+static_assert(PROD_WARPS <= STAGES * SUB, "every producer warp needs a sub-tile of its own");
 
 // shared-memory plan of k_leaf_score (offsets from a 1024-aligned base)
 constexpr int SM_STAGES = 0;
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full + s, 32);  // the lanes of the stage's producer warp
+            mbar_init(full + s, 32 * SUB);  // the lanes of the stage's SUB producer warps
             mbar_init(empty + s, 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -330,15 +332,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const int item_lo = *A.item_lo, item_hi = *A.item_hi;
-    const int KC = (F.d + BK - 1) / BK;
+    const int KC = (F.d + SUB * BK - 1) / (SUB * BK);  // stages per row tile
     const uint32_t stage0 = smem_u32(sm + SM_STAGES);
 
     if (warp >= 4 && warp < MMA_WARP) {
         // ------------------------------------------------ producers: leaf rows and query parts
-        // Stage g of the CTA's stream belongs to producer warp g % PROD_WARPS.  The warp copies
-        // the whole stage (lane: one 16-byte column chunk of every fourth row), waits for its own
-        // copies, makes them visible to the tensor cores and signals the stage full: no stage
-        // waits for another one's copies.
+        // Sub-tile h = SUB g + u of the CTA's stream (stage g, k-step u) belongs to producer warp
+        // h % PROD_WARPS.  The warp copies the whole sub-tile (lane: one 16-byte column chunk of
+        // every fourth row), waits for its own copies, makes them visible to the tensor cores and
+        // arrives on the stage's full barrier: no sub-tile waits for another one's copies.
         const int pw = warp - 4;
         const int c = lane & 7, r0 = lane >> 3;  // column chunk; rows r0, r0 + 4, ...
         uint32_t it = 0;                          // stages of the CTA's earlier chunks
@@ -353,12 +355,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                 const int j = r0 + 4 * i;
                 qid[i] = j < nq ? A.qlist[q0pos + j] : -1;
             }
-            const int nst = (rows + BM - 1) / BM * KC;
+            const int nst = (rows + BM - 1) / BM * KC * SUB;  // the chunk's sub-tiles
             int ids[BM / 4];  // point ids of the lane's rows of tile `cur`
             int cur = -1;
-            for (int st = (int)((pw + PROD_WARPS - it % PROD_WARPS) % PROD_WARPS); st < nst; st += PROD_WARPS) {
-                const uint32_t g = it + st;
-                const uint32_t s = g % STAGES;
+            for (int sh = (int)((pw + PROD_WARPS - it % PROD_WARPS) % PROD_WARPS); sh < nst; sh += PROD_WARPS) {
+                const uint32_t h = it + sh;
+                const uint32_t g = h / SUB, s = g % STAGES;
+                const int st = sh / SUB, u = sh - st * SUB;
                 const int mt = st / KC, kc = st - mt * KC;
                 if (mt != cur) {
                     cur = mt;
@@ -369,9 +372,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                     }
                 }
                 if (!mbar_wait(empty + s, ((g / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                const int col = kc * BK + c * 8;
+                const int kcol = (kc * SUB + u) * BK;
+                if (kcol >= F.d) {  // past the row: nothing to load, the MMA skips this sub-tile
+                    mbar_arrive(full + s);
+                    continue;
+                }
+                const int col = kcol + c * 8;
                 const int nb = max(0, min(16, (F.d - col) * 2));
-                const uint32_t sa = stage0 + s * STAGE_BYTES;
+                const uint32_t sa = stage0 + s * STAGE_BYTES + u * SUBTILE_BYTES;
 #pragma unroll
                 for (int i = 0; i < BM / 4; ++i) {
                     const int r = r0 + 4 * i;
@@ -417,8 +425,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                     const uint32_t d_tmem = tmem_base + buf * MMA_N;
                     for (int kc = 0; kc < KC; ++kc) {
                         if (!mbar_wait(full + s, ph, abort_flag)) { ok = false; break; }
-                        const uint64_t off = (uint64_t)((s * STAGE_BYTES) >> 4);
-                        mma_stage(d_tmem, da0 + off, db0 + off, kc != 0);
+#pragma unroll
+                        for (int u = 0; u < SUB; ++u) {
+                            if ((kc * SUB + u) * BK >= F.d) break;
+                            const uint64_t off = (uint64_t)((s * STAGE_BYTES + u * SUBTILE_BYTES) >> 4);
+                            mma_stage(d_tmem, da0 + off, db0 + off, (kc | u) != 0);
+                        }
                         mma_commit(empty + s);
                         if (++s == STAGES) { s = 0; ph ^= 1; }
                     }
