@@ -50,9 +50,9 @@ namespace {
 constexpr int NQ = 16;           // queries per chunk (the MMA's N is 2 NQ: parts hi and lo)
 constexpr int BM = 128;          // leaf rows per tile: the MMA's M, one tensor-memory lane each
 constexpr int BK = 64;           // bf16 values per sub-tile: one 128-byte swizzled row
-constexpr int SUB = 2;           // sub-tiles per pipeline stage: one wait and one release per SUB k-steps
-constexpr int STAGES = 5;        // shared-memory pipeline depth
-constexpr int PROD_WARPS = 10;   // producer warps; each loads whole sub-tiles, one at a time
+constexpr int SUB = 3;           // sub-tiles per pipeline stage: one wait and one release per SUB k-steps
+constexpr int STAGES = 3;        // shared-memory pipeline depth
+constexpr int PROD_WARPS = 9;    // producer warps; each loads whole sub-tiles, one at a time
 constexpr int R_MAX = 32;        // longest shortlist per (query, tree): one key per lane
 constexpr int A_BYTES = BM * 128;
 constexpr int B_BYTES = NQ * 128;
