@@ -229,12 +229,12 @@ def query_bytes(gf, F, prec, C, R, d, k, leaves=0):
     return rows + rerank + d * 4 + positions * 4 + 12 * k
 
 
-def leaf_bytes(gf, F, Qg, R, k):
+def leaf_bytes(gf, F, Qg, R, k, fp32=False):
     """Algorithmic bytes of one leaf-major batch: every chunk (a (tree, leaf) bucket cut into groups
-    of at most 16 queries) reads its leaf's bf16 rows with their ids and |x~|^2 once; plus the query
-    (read, split into bf16 parts), the (query, tree) shortlists written and merged, the float32
-    rerank rows and the results.  The query parts re-read per row tile come from L2 (a few tens of
-    MB in all) and are not counted."""
+    of at most 16 queries) reads its leaf's rows once -- bf16 with their ids and |x~|^2, or float32
+    with their ids; plus the query (read, split or padded), the (query, tree) lists written and
+    merged, the float32 rerank rows (bf16 screen) and the results.  The query rows re-read per row
+    tile come from L2 (a few tens of MB in all) and are not counted."""
     import torch
     inf = F.info
     m, T, L = Qg.shape[0], inf.T, inf.L
@@ -245,8 +245,12 @@ def leaf_bytes(gf, F, Qg, R, k):
     b = torch.arange(T << L, device=Qg.device) & ((1 << L) - 1)
     rows = ((b + 1) * inf.n >> L) - (b * inf.n >> L)
     ldb, ldx = (inf.d + 7) // 8 * 8, (inf.d + 3) // 4 * 4
-    row_bytes = int((chunks * rows).sum()) * (ldb * 2 + 8)
-    other = m * inf.d * 4 * 2 + m * ldb * 2 * 2 + m * T * R * 8 * 2 + m * R * ldx * 4 + m * k * 12
+    if fp32:
+        row_bytes = int((chunks * rows).sum()) * (ldx * 4 + 4)
+        other = m * inf.d * 4 + m * ldx * 4 * 2 + m * T * R * 8 * 2 + m * k * 12
+    else:
+        row_bytes = int((chunks * rows).sum()) * (ldb * 2 + 8)
+        other = m * inf.d * 4 * 2 + m * ldb * 2 * 2 + m * T * R * 8 * 2 + m * R * ldx * 4 + m * k * 12
     return row_bytes + other, int(chunks.sum())
 
 
@@ -300,9 +304,9 @@ def ours(args):
         C = float(nc.double().mean())
         entry["cand_per_query"] = round(C, 1)
         leaves = gf.leaf_budget(F, checks) if checks else 0
-        runs = [("fp32", gf.GF_FP32, gf.GF_ALGO_STREAM), ("bf16_stream", gf.GF_BF16_RERANK, gf.GF_ALGO_STREAM)]
+        runs = [("fp32_stream", gf.GF_FP32, gf.GF_ALGO_STREAM), ("bf16_stream", gf.GF_BF16_RERANK, gf.GF_ALGO_STREAM)]
         if not checks:  # the leaf-major path runs the one-leaf-per-tree search
-            runs.append(("bf16_leaf", gf.GF_BF16_RERANK, gf.GF_ALGO_LEAF))
+            runs += [("fp32_leaf", gf.GF_FP32, gf.GF_ALGO_LEAF), ("bf16_leaf", gf.GF_BF16_RERANK, gf.GF_ALGO_LEAF)]
         tuned = {}
         for name, prec, algo in runs:
             if prec not in tuned:
@@ -316,7 +320,7 @@ def ours(args):
             r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
             mean_ms = statistics.mean(ms)
             if algo == gf.GF_ALGO_LEAF:
-                lb, nchunks = leaf_bytes(gf, F, Qg, R, k)
+                lb, nchunks = leaf_bytes(gf, F, Qg, R if prec != gf.GF_FP32 else k, k, prec == gf.GF_FP32)
                 bpq = lb / m
             else:
                 bpq, nchunks = bytes_per_query(F, prec, C, R, leaves), None
@@ -330,8 +334,9 @@ def ours(args):
             else:
                 entry[name].update(warps_per_cta=tr["warps"], ctas_per_sm=tr["ctas_per_sm"],
                                    rows_in_flight=tr["rows_in_flight"])
-        bf = [entry[nm] for nm in ("bf16_stream", "bf16_leaf") if nm in entry]
-        entry["bf16"] = max(bf, key=lambda e: e["qps"])
+        for prec_name in ("fp32", "bf16"):
+            cands = [entry[nm] for nm in (prec_name + "_stream", prec_name + "_leaf") if nm in entry]
+            entry[prec_name] = max(cands, key=lambda e: e["qps"])
         return F, entry
 
     Fh, head = run_forest(HEADLINE["T"], HEADLINE["leaf_size"], args.tune_sample)

@@ -67,12 +67,14 @@ typedef struct gf_rand_params {
                             8 * next_pow2(T * max_leaf) bytes of shared memory per CTA */
 #define GF_ALGO_STREAM 2 /* candidates de-duplicated through a per-CTA bitmap over the point ids
                             in device memory ("seen" array, Sec. 2.3); any candidate count */
-#define GF_ALGO_LEAF 3   /* leaf-major batch (bf16 screen, one leaf per tree): the (query, tree)
-                            pairs are grouped by the leaf they reach, each leaf's rows are read once
-                            per group of up to 32 queries and scored against all of them on the
-                            tensor cores; per query the trees' shortlists are merged, de-duplicated
-                            by id and reranked in float32.  R <= 32, T * R <= 8192,
-                            T * 2^L <= 2^22; the workspace need not be zero and is left zero */
+#define GF_ALGO_LEAF 3   /* leaf-major batch (one leaf per tree): the (query, tree) pairs are
+                            grouped by the leaf they reach, and each leaf's rows are read once per
+                            group of up to 16 queries and scored against all of them -- the bf16
+                            screen on the tensor cores, float32 (direct form) on the CUDA cores;
+                            per query the trees' lists are merged and de-duplicated by id, and the
+                            screen's R best reranked in float32.  bf16: R <= 32; float32: k <= 32;
+                            T * R <= 8192, T * 2^L <= 2^22; the workspace need not be zero and is
+                            left zero */
 
 /* Order in which the streaming kernel's CTAs take the queries of a batch.  Results do not depend
  * on it; throughput does: queries that reach the same leaf of tree 0 share most candidates, and

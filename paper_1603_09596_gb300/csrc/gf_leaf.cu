@@ -277,7 +277,8 @@ struct LeafArgs {
     const int *bcnt;       // queries per bucket
     const int *boff;       // first position of each bucket in qlist
     const int *qlist;      // query ids grouped by bucket
-    const __nv_bfloat16 *qhi, *qlo;  // [m][ldb] query parts
+    const __nv_bfloat16 *qhi, *qlo;  // [m][ldb] query parts (bf16 screen)
+    const float *qf;                 // [m][ldx] the queries, rows padded (float32 kernel)
     unsigned long long *part;        // [m][T][R] screened keys
     unsigned long long *tau;         // [m] upper bound on each query's R-th best key
     int R;
@@ -527,6 +528,174 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                      : "memory");
 }
 
+// ---------------------------------------------------------------- float32 scoring (CUDA cores)
+//
+// The plain float32 search through the same regrouping: each chunk's leaf rows against its
+// queries in the direct form sum_j (q_j - x_j)^2, float32 arithmetic (packed f32x2 pairs, rounded
+// per lane as the scalar instructions), on the CUDA cores.  Row tiles of 256 rows: lane l of warp w
+// owns rows 64 w + l and 64 w + 32 + l of the tile and accumulates every query of the chunk for
+// them.  The rows stream through a two-stage cp.async ring of 32-float slabs (128 bytes per row);
+// the 16-byte chunk c of row r sits at chunk c ^ (r & 7), so a warp's 16-byte loads of 32
+// consecutive rows fall on distinct banks.  The queries' slabs sit beside them (a padded float32
+// copy of the batch) and are read by broadcast.  Keys are (distance bits, id); the per-warp lists,
+// the bound tau_q and the per-chunk merge are those of the bf16 kernel, with the k best kept per
+// (query, tree); the lists are merged in the ring's memory, idle between chunks.
+namespace f32k {
+constexpr int THREADS = 128;
+constexpr int ROWS = 256;
+constexpr int KS = 32;                          // floats per slab: one 128-byte row segment
+constexpr int STAGES = 2;
+constexpr int X_BYTES = ROWS * KS * 4;          // the tile's rows of one slab
+constexpr int Q_BYTES = NQ * KS * 4;            // the chunk's queries of one slab
+constexpr int STAGE_BYTES = X_BYTES + Q_BYTES;
+constexpr int WL_BYTES = 4 * NQ * 32 * 8;       // the four warps' lists
+constexpr int SMEM = STAGES * STAGE_BYTES;
+static_assert(THREADS / 8 == NQ, "copy duty: eight threads per query row");
+static_assert(WL_BYTES <= SMEM, "the lists reuse the ring");
+__device__ __forceinline__ int swz(int r, int c) { return c ^ (r & 7); }
+}  // namespace f32k
+
+__global__ void __launch_bounds__(f32k::THREADS, 2) k_leaf_f32(ForestView F, LeafArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *wl = reinterpret_cast<unsigned long long *>(smem_raw);  // between chunks only
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int item_lo = *A.item_lo, item_hi = *A.item_hi;
+    const int NS = (F.d + f32k::KS - 1) / f32k::KS;  // slabs per row tile
+    const int R = A.R;
+    int RL = 1;
+    while (RL < R) RL <<= 1;
+    const int cc = tid & 7, cr = tid >> 3;  // copy duty: 16-byte chunk cc of rows cr + 16 i, query cr
+    const uint32_t sbase = smem_u32(smem_raw);
+    for (int w = item_lo + blockIdx.x; w < item_hi; w += gridDim.x) {
+        int t, rows, q0pos, nq;
+        long long lo;
+        chunk_of(F, A, w, t, lo, rows, q0pos, nq);
+        const int ng = (nq + 3) >> 2;  // groups of four queries
+        const int qid_c = cr < nq ? A.qlist[q0pos + cr] : -1;
+        const int my_qid = lane < nq ? A.qlist[q0pos + lane] : 0;
+        const unsigned long long my_tau = lane < nq ? __ldcg(A.tau + my_qid) : KEY_NONE;
+        unsigned long long lst[NQ];
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) lst[j] = KEY_NONE;
+        const int *perm_leaf = F.perm + (size_t)t * F.n + lo;
+        const int MT = (rows + f32k::ROWS - 1) / f32k::ROWS;
+        for (int mt = 0; mt < MT; ++mt) {
+            int ids[f32k::ROWS / 16];
+#pragma unroll
+            for (int i = 0; i < f32k::ROWS / 16; ++i) {
+                const int r = mt * f32k::ROWS + cr + 16 * i;
+                ids[i] = r < rows ? __ldg(perm_leaf + r) : -1;
+            }
+            auto load_slab = [&](int sl, int stg) {
+                const int col = sl * f32k::KS + cc * 4;
+                const int nbytes = max(0, min(16, (F.d - col) * 4));
+                const uint32_t xs = sbase + stg * f32k::STAGE_BYTES;
+#pragma unroll
+                for (int i = 0; i < f32k::ROWS / 16; ++i) {
+                    const int r = cr + 16 * i;
+                    const bool live = ids[i] >= 0 && nbytes > 0;
+                    const float *src = live ? F.x + (size_t)ids[i] * F.ldx + col : F.x;
+                    cp_async16(xs + r * (f32k::KS * 4) + (f32k::swz(r, cc) << 4), src, live ? nbytes : 0);
+                }
+                {
+                    const bool live = qid_c >= 0 && nbytes > 0;
+                    const float *src = live ? A.qf + (size_t)qid_c * F.ldx + col : A.qf;
+                    cp_async16(xs + f32k::X_BYTES + cr * f32k::KS * 4 + cc * 16, src, live ? nbytes : 0);
+                }
+                cp_async_commit();
+            };
+            unsigned long long acc[2][NQ];  // packed (even, odd) partial sums per (row, query)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) acc[a][j] = 0ull;
+            // double buffer: slab sl + 1 is requested while slab sl is scored
+            load_slab(0, 0);
+            for (int sl = 0; sl < NS; ++sl) {
+                if (sl + 1 < NS) load_slab(sl + 1, (sl + 1) & 1);
+                else cp_async_commit();
+                cp_async_wait<1>();
+                __syncthreads();
+                const unsigned char *xs = smem_raw + (sl & 1) * f32k::STAGE_BYTES;
+                const float *qs = reinterpret_cast<const float *>(xs + f32k::X_BYTES);
+                const int r0 = 64 * warp + lane, r1 = r0 + 32;
+#pragma unroll 2
+                for (int c4 = 0; c4 < f32k::KS / 4; ++c4) {
+                    const float4 x0 = *reinterpret_cast<const float4 *>(xs + r0 * (f32k::KS * 4) + (f32k::swz(r0, c4) << 4));
+                    const float4 x1 = *reinterpret_cast<const float4 *>(xs + r1 * (f32k::KS * 4) + (f32k::swz(r1, c4) << 4));
+                    const unsigned long long a01 = pk(x0.x, x0.y), a23 = pk(x0.z, x0.w);
+                    const unsigned long long b01 = pk(x1.x, x1.y), b23 = pk(x1.z, x1.w);
+#pragma unroll
+                    for (int g = 0; g < NQ / 4; ++g) {
+                        if (g < ng) {
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const int j = 4 * g + jj;
+                                const float4 qv = *reinterpret_cast<const float4 *>(qs + j * f32k::KS + c4 * 4);
+                                const unsigned long long q01 = pk(qv.x, qv.y), q23 = pk(qv.z, qv.w);
+                                unsigned long long e = sub2(q01, a01);
+                                acc[0][j] = fma2(e, e, acc[0][j]);
+                                e = sub2(q23, a23);
+                                acc[0][j] = fma2(e, e, acc[0][j]);
+                                e = sub2(q01, b01);
+                                acc[1][j] = fma2(e, e, acc[1][j]);
+                                e = sub2(q23, b23);
+                                acc[1][j] = fma2(e, e, acc[1][j]);
+                            }
+                        }
+                    }
+                }
+                __syncthreads();  // the stage is refilled two slabs later
+            }
+            // the tile's distances: the warp's 64 rows against every query of the chunk
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int r = mt * f32k::ROWS + 64 * warp + 32 * a + lane;
+                const bool valid = r < rows;
+                const int id = valid ? __ldg(perm_leaf + r) : 0;
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) {
+                    if (j < nq) {
+                        const float2 s = upk(acc[a][j]);
+                        const unsigned long long key = valid ? make_key(s.x + s.y, id) : KEY_NONE;
+                        const unsigned long long thr =
+                            umin64(__shfl_sync(FULL, lst[j], R - 1), __shfl_sync(FULL, my_tau, j));
+                        const unsigned bl = __ballot_sync(FULL, key < thr);
+                        if (bl) lst[j] = list_add(lst[j], key, bl, R, RL);
+                    }
+                }
+            }
+        }
+        // the chunk is done: merge the four warps' lists; each query's R best of this leaf
+#pragma unroll
+        for (int j = 0; j < NQ; ++j)
+            if (j < nq) wl[(warp * NQ + j) * 32 + lane] = lst[j];
+        __syncthreads();
+        for (int j = warp; j < nq; j += 4) {
+            unsigned long long a = wl[(0 * NQ + j) * 32 + lane], b = wl[(1 * NQ + j) * 32 + lane];
+            unsigned long long c = wl[(2 * NQ + j) * 32 + lane], d = wl[(3 * NQ + j) * 32 + lane];
+            if (lane >= RL) a = b = c = d = KEY_NONE;
+            const unsigned long long best = warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL);
+            const int qid = A.qlist[q0pos + j];
+            if (lane < R) A.part[((size_t)qid * F.T + t) * R + lane] = best;
+            const unsigned long long kth = __shfl_sync(FULL, best, R - 1);
+            if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + qid, kth);
+        }
+        __syncthreads();  // the lists are rewritten by the next chunk
+    }
+}
+
+// q -> a float32 copy with rows padded to ldx (16-byte aligned rows for the copies)
+__global__ void k_qpad(const float *__restrict__ Q, long long m, int d, int ldx, float *qf) {
+    const long long total = m * ldx;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long i = g / ldx;
+        const int j = (int)(g - i * ldx);
+        qf[g] = j < d ? Q[i * d + j] : 0.f;
+    }
+}
+
 // ---------------------------------------------------------------- batch regrouping
 
 __global__ void k_bucket_count(const int *__restrict__ leaf, long long pairs, int T, int L, int *bcnt) {
@@ -615,11 +784,11 @@ __global__ void k_qsplit(const float *__restrict__ Q, long long m, int d, int ld
 
 // ---------------------------------------------------------------- merge + rerank
 
-// Per query: the T lists of R screened keys -> distinct ids -> the R best -> float32 rerank ->
-// k nearest.  One CTA per query at a time.
+// Per query: the T lists of R keys -> distinct ids -> the R best -> (screened keys: float32
+// rerank) -> k nearest.  One CTA per query at a time.
 template <int NCF>
 __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *__restrict__ Q, long long m, int k,
-                                                    int R, const unsigned long long *__restrict__ part,
+                                                    int R, int rerank, const unsigned long long *__restrict__ part,
                                                     long long *ids, float *dists) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TR = F.T * R;
@@ -650,12 +819,16 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
                 atomicAdd(&nshort, 1);
             }
         }
-        load_query(Q + qi * F.d, F.d, qs);
+        if (rerank) load_query(Q + qi * F.d, F.d, qs);
         __syncthreads();
         const int C = nshort;  // the valid keys are a prefix of the sorted list
-        rescore_f32<NCF>(F, qs, sid, C, a);
-        sort_keys(a, C);
-        write_topk(a, C, k, ids + qi * k, dists + qi * k);
+        if (rerank) {
+            rescore_f32<NCF>(F, qs, sid, C, a);
+            sort_keys(a, C);
+            write_topk(a, C, k, ids + qi * k, dists + qi * k);
+        } else {  // the keys are float32 distances already, in order
+            write_topk(b, C, k, ids + qi * k, dists + qi * k);
+        }
         __syncthreads();
     }
 }
@@ -704,10 +877,14 @@ int order_of(int order) { return order == GF_ORDER_GIVEN ? GF_ORDER_GIVEN : GF_O
 
 const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R,
                                 const QueryExtra &x) {
-    if (precision != GF_BF16_RERANK) return "the leaf-major path runs the bf16 screen only";
-    if (!F->xb || !F->xbn) return "the forest has no bf16 copy";
+    if (precision != GF_BF16_RERANK && precision != GF_FP32) return "the leaf-major path runs float32 or the bf16 screen";
+    if (precision == GF_BF16_RERANK && (!F->xb || !F->xbn)) return "the forest has no bf16 copy";
     if (x.leaf_budget > 0) return "the leaf-major path runs the one-leaf-per-tree search only";
     if (x.ncand_out) return "candidate counts are reported by the streaming kernel only";
+    if (precision == GF_FP32) {
+        if (k > R_MAX) return "the leaf-major float32 path keeps at most 32 per (query, tree): k <= 32";
+        R = k;
+    }
     if (R < 1 || R > R_MAX) return "the leaf-major path keeps a shortlist of 1..32";
     if (k > R) return "k exceeds the shortlist";
     if ((int64_t)F->T * R > MAX_KEYS) return "T * R above 8192";
@@ -723,13 +900,18 @@ bool gf_leaf_preferred(const gf_forest *F, int64_t m, int32_t k, int32_t precisi
     return gf_leaf_unsupported(F, m, k, precision, R, x) == nullptr && (m >> F->L) >= LEAF_MIN_SHARE;
 }
 
-int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t R, int32_t order) {
-    return (int64_t)leaf_workspace(F, m, std::max(1, std::min(R, R_MAX)), order_of(order)).total;
+int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order) {
+    // float32 keeps k <= 32 per (query, tree): size for the most
+    const int len = precision == GF_FP32 ? R_MAX : std::max(1, std::min(R, R_MAX));
+    return (int64_t)leaf_workspace(F, m, len, order_of(order)).total;
 }
 
-int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int32_t order,
-                   cudaStream_t st, int64_t *ids, float *dists, void *workspace, int64_t workspace_bytes) {
+int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision, int32_t R,
+                   int32_t order, cudaStream_t st, int64_t *ids, float *dists, void *workspace,
+                   int64_t workspace_bytes) {
     order = order_of(order);
+    const bool f32 = precision == GF_FP32;
+    if (f32) R = k;  // the exact distances: the k best of every (query, tree) suffice
     const LeafWorkspace W = leaf_workspace(F, m, R, order);
     char *ws = (char *)workspace;
     bool own = false;
@@ -776,11 +958,15 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, F->L, locality, kcnt);
     k_scan<<<1, 1024, 0, st>>>(kcnt, nk, koff);
     k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, F->L, locality, koff, kfill, items);
-    k_qsplit<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldb, qhi, qlo);
+    // float32: the padded query copy takes the place of the two bf16 parts (as large together)
+    float *qf = (float *)(ws + W.qhi);
+    if (f32) k_qpad<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldx, qf);
+    else k_qsplit<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldb, qhi, qlo);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major regrouping");
 
-    e = cudaFuncSetAttribute(k_leaf_score, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(k_leaf_score)");
+    e = f32 ? cudaFuncSetAttribute(k_leaf_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, f32k::SMEM)
+            : cudaFuncSetAttribute(k_leaf_score, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(leaf-major scoring)");
     LeafArgs A;
     A.items = items;
     A.bcnt = bcnt;
@@ -788,17 +974,18 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     A.qlist = qlist;
     A.qhi = qhi;
     A.qlo = qlo;
+    A.qf = qf;
     A.part = part;
     A.tau = tau;
     A.R = R;
     // the chunks of tree 0 (keys below 2^L) set every query's bound; then all the others
-    A.item_lo = koff;
-    A.item_hi = koff + (1 << F->L);
-    k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
-    A.item_lo = koff + (1 << F->L);
-    A.item_hi = koff + nk;
-    k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_leaf_score launch");
+    for (int wave = 0; wave < 2; ++wave) {
+        A.item_lo = wave == 0 ? koff : koff + (1 << F->L);
+        A.item_hi = wave == 0 ? koff + (1 << F->L) : koff + nk;
+        if (f32) k_leaf_f32<<<F->num_sms * 2, f32k::THREADS, f32k::SMEM, st>>>(view_of(F), A);
+        else k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major scoring launch");
 
     const size_t msmem = merge_smem(F, R);
     const unsigned mg = (unsigned)std::min<long long>(m, (long long)F->num_sms * 16);
@@ -809,7 +996,7 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
             (e = cudaFuncSetAttribute(k_leaf_merge<NCV>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                       (int)msmem)) != cudaSuccess)                                       \
             return fail(e, "cudaFuncSetAttribute(k_leaf_merge)");                                        \
-        k_leaf_merge<NCV><<<mg, 128, msmem, st>>>(view_of(F), Q, m, k, R, part, (long long *)ids, dists); \
+        k_leaf_merge<NCV><<<mg, 128, msmem, st>>>(view_of(F), Q, m, k, R, !f32, part, (long long *)ids, dists); \
     }
     GF_MERGE(1) GF_MERGE(2) GF_MERGE(4) GF_MERGE(8) GF_MERGE(0)
 #undef GF_MERGE

@@ -244,6 +244,7 @@ extern "C" int gf_server_create(gf_forest *const *forests, int32_t nforests, con
         qo.rerank_R = o.rerank_R;
         qo.checks = o.checks;
         qo.eps = o.eps;
+        qo.algo = GF_ALGO_STREAM;  // the kernel launch_batch runs
         int64_t b = 0;
         int r = gf_query_workspace_size(forests[i], o.max_batch, &qo, &b);
         if (r) { delete S; return r; }

@@ -16,7 +16,7 @@ import torch
 import oracle
 import synth
 from oracle import screen
-from parity import assert_screened_close, candidate_sets
+from parity import assert_screened_close, assert_topk_close, candidate_sets
 
 pytestmark = pytest.mark.gpu
 
@@ -161,11 +161,35 @@ def test_leaf_reflected_forest(gf):
     assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
 
 
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("k", [1, 10])
+def test_leaf_fp32_matches_oracle(gf, name, k):
+    # the plain float32 search through the leaf-major path: exact distances, ids up to near-ties
+    X, Q, F = case(name)
+    G = gpu_forest(gf, X, F)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, algo=gf.GF_ALGO_LEAF)
+    oi, od = oracle.search(F, X, Q, k)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+    assert gf.gf_kernel_status() == 0
+
+
+def test_leaf_fp32_agrees_with_streaming(gf):
+    # the same float32 search by two kernels: distances within 1e-5 relative, ids equal up to ties
+    X, Q, F = case("shared")
+    G = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    a = gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_LEAF)
+    b = gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_STREAM)
+    assert_topk_close(X, Q, a[0].cpu().numpy(), a[1].cpu().numpy(), b[0].cpu().numpy(),
+                      b[1].cpu().numpy().astype(np.float64))
+
+
 def test_leaf_rejects_what_it_does_not_run(gf):
     X, Q, F = case("tiny")
     G = gpu_forest(gf, X, F)
+    gf.gf_forest_add_screen(G, gf.GF_FP8_RERANK)
     Qg = torch.from_numpy(Q).cuda()
-    for kw in (dict(precision=gf.GF_FP32),                                   # float32 scoring
+    for kw in (dict(precision=gf.GF_FP8_RERANK),                             # the fp8 screen
                dict(precision=gf.GF_BF16_RERANK, rerank_R=33),               # shortlist above 32
                dict(precision=gf.GF_BF16_RERANK, rerank_R=16, checks=64)):  # priority search
         with pytest.raises(gf.GFError) as e:
