@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
 // (query, tree); the lists are merged in the ring's memory, idle between chunks.
 namespace f32k {
 constexpr int THREADS = 128;
+constexpr int CTAS_PER_SM = 3;
 constexpr int ROWS = 256;
 constexpr int KS = 32;                          // floats per slab: one 128-byte row segment
 constexpr int STAGES = 2;
@@ -555,7 +556,7 @@ static_assert(WL_BYTES <= SMEM, "the lists reuse the ring");
 __device__ __forceinline__ int swz(int r, int c) { return c ^ (r & 7); }
 }  // namespace f32k
 
-__global__ void __launch_bounds__(f32k::THREADS, 2) k_leaf_f32(ForestView F, LeafArgs A) {
+__global__ void __launch_bounds__(f32k::THREADS, f32k::CTAS_PER_SM) k_leaf_f32(ForestView F, LeafArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long *wl = reinterpret_cast<unsigned long long *>(smem_raw);  // between chunks only
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -621,18 +622,18 @@ __global__ void __launch_bounds__(f32k::THREADS, 2) k_leaf_f32(ForestView F, Lea
                 const int r0 = 64 * warp + lane, r1 = r0 + 32;
 #pragma unroll 2
                 for (int c4 = 0; c4 < f32k::KS / 4; ++c4) {
-                    const float4 x0 = *reinterpret_cast<const float4 *>(xs + r0 * (f32k::KS * 4) + (f32k::swz(r0, c4) << 4));
-                    const float4 x1 = *reinterpret_cast<const float4 *>(xs + r1 * (f32k::KS * 4) + (f32k::swz(r1, c4) << 4));
-                    const unsigned long long a01 = pk(x0.x, x0.y), a23 = pk(x0.z, x0.w);
-                    const unsigned long long b01 = pk(x1.x, x1.y), b23 = pk(x1.z, x1.w);
+                    // four floats as two packed pairs (low half first): no repacking
+                    const ulonglong2 x0 = *reinterpret_cast<const ulonglong2 *>(xs + r0 * (f32k::KS * 4) + (f32k::swz(r0, c4) << 4));
+                    const ulonglong2 x1 = *reinterpret_cast<const ulonglong2 *>(xs + r1 * (f32k::KS * 4) + (f32k::swz(r1, c4) << 4));
+                    const unsigned long long a01 = x0.x, a23 = x0.y, b01 = x1.x, b23 = x1.y;
 #pragma unroll
                     for (int g = 0; g < NQ / 4; ++g) {
                         if (g < ng) {
 #pragma unroll
                             for (int jj = 0; jj < 4; ++jj) {
                                 const int j = 4 * g + jj;
-                                const float4 qv = *reinterpret_cast<const float4 *>(qs + j * f32k::KS + c4 * 4);
-                                const unsigned long long q01 = pk(qv.x, qv.y), q23 = pk(qv.z, qv.w);
+                                const ulonglong2 qv = *reinterpret_cast<const ulonglong2 *>(qs + j * f32k::KS + c4 * 4);
+                                const unsigned long long q01 = qv.x, q23 = qv.y;
                                 unsigned long long e = sub2(q01, a01);
                                 acc[0][j] = fma2(e, e, acc[0][j]);
                                 e = sub2(q23, a23);
@@ -982,7 +983,7 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     for (int wave = 0; wave < 2; ++wave) {
         A.item_lo = wave == 0 ? koff : koff + (1 << F->L);
         A.item_hi = wave == 0 ? koff + (1 << F->L) : koff + nk;
-        if (f32) k_leaf_f32<<<F->num_sms * 2, f32k::THREADS, f32k::SMEM, st>>>(view_of(F), A);
+        if (f32) k_leaf_f32<<<F->num_sms * f32k::CTAS_PER_SM, f32k::THREADS, f32k::SMEM, st>>>(view_of(F), A);
         else k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major scoring launch");
