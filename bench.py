@@ -492,7 +492,8 @@ def profile(args):
         gf.gf_forest_add_screen(F, prec)
     algo = {"stream": gf.GF_ALGO_STREAM, "sort": gf.GF_ALGO_SORT, "leaf": gf.GF_ALGO_LEAF}[args.profile_algo]
     kw = dict(precision=prec, rerank_R=args.profile_R, warps_per_cta=args.profile_warps,
-              ctas_per_sm=args.profile_ctas, algo=algo, rows_in_flight=args.profile_rows)
+              ctas_per_sm=args.profile_ctas, algo=algo, rows_in_flight=args.profile_rows,
+              checks=args.profile_checks)
     gf.gf_query(F, Qg, 10, **kw)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -503,6 +504,7 @@ def profile(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile": True, "n": args.n, "d": args.d, "m": args.m, "T": args.T,
                       "leaf_size": args.leaf_size, "precision": args.precision, "algo": args.profile_algo,
+                      "checks": args.profile_checks,
                       "ms_per_launch": a.elapsed_time(b) / args.steps, "kernel_status": gf.gf_kernel_status()}))
 
 
@@ -725,6 +727,7 @@ def main():
     ap.add_argument("--source-hash", action="store_true", help="print the query kernel's source hash")
     ap.add_argument("--profile-ctas", type=int, default=0)
     ap.add_argument("--profile-algo", default="stream", choices=["stream", "sort", "leaf"])
+    ap.add_argument("--profile-checks", type=int, default=0, help="leaf checks c (priority search) of the profile launches")
     ap.add_argument("--serve", action="store_true", help="serving workload (six forests, Poisson load)")
     ap.add_argument("--highd", action="store_true", help="d = 10^4 workload: fp8 / bf16 / fp32")
     ap.add_argument("--klein", action="store_true", help="noisy Klein bottle in R^100, 10^6 points")

@@ -1,6 +1,7 @@
-// gf_leaf.cu -- the leaf-major batched query path (GF_ALGO_LEAF): the bf16 screen + float32 rerank
-// of the one-leaf-per-tree search (Alg. 2 with c = T), regrouped so that every leaf's points are
-// read once per group of queries that reach it.
+// gf_leaf.cu -- the leaf-major batched query path (GF_ALGO_LEAF): the one-leaf-per-tree search
+// (Alg. 2 with c = T), bf16 screen + float32 rerank on the tensor cores or plain float32 on the CUDA
+// cores (k_leaf_f32, further down), regrouped so that every leaf's points are read once per group
+// of queries that reach it.
 //
 // A query's candidates are the points of the T leaves it reaches (Eq. 1); its answer is the k
 // nearest of their union.  In a large batch many queries reach the same leaf of a tree (10^4
@@ -13,8 +14,10 @@
 //      different trees that cover the same region of the data run at about the same time and find
 //      each other's rows in L2;
 //   4. score (k_leaf_score): one persistent CTA per SM walks the chunks.  A chunk's leaf rows are
-//      staged in shared memory 128 at a time and multiplied against the chunk's queries on the
-//      tensor cores (tcgen05.mma, bf16 inputs, float32 accumulators in tensor memory).  The screened
+//      staged in shared memory 128 at a time, in stages of three 64-wide k-steps, each k-step
+//      gathered by its own producer warp, and multiplied against the chunk's queries on the tensor
+//      cores (tcgen05.mma, M = 128 rows, N = the queries' hi and lo parts, bf16 inputs, float32
+//      accumulators in tensor memory, issued by one thread).  The screened
 //      score of point x for query q is |x~|^2 - 2 x~.q, which orders the points of one query as
 //      |x~ - q|^2 does (the two differ by |q|^2).  x~ is the bf16 copy of the forest; the query
 //      enters as two bf16 parts hi + lo (hi = bf16(q), lo = bf16(q - hi)), i.e. with about 16

@@ -7,7 +7,9 @@
 //   * then, while fewer than `budget` leaves were checked, the entry of smallest
 //     (key, tree, node) is taken from the queue and descended the same way to one more leaf.
 // The keys are computed in float64 (the difference of two floats is exact there), so the order,
-// including ties, is exactly the CPU oracle's.
+// including ties, is exactly the CPU oracle's.  A key is non-negative, so its IEEE bits order as the
+// value does: the queue compares the bits as 64-bit integers (GB300's float64 compare rate is a
+// small fraction of its integer rate).
 //
 // One warp per query.  The queue is a sorted array in shared memory; the entries a descent pushes
 // (at most L <= 30, or one per tree in the first phase) are merged into it by the warp.  Entries
@@ -24,7 +26,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int PRIO_WARPS = 4;  // at most this many warps (queries) per CTA
 
 struct PQE {
-    double key;
+    unsigned long long key;  // bits of the float64 key |q_s - v| (>= 0)
     int tree;
     int node;
 };
@@ -35,9 +37,13 @@ __device__ __forceinline__ bool pq_less(const PQE &a, const PQE &b) {
     return a.node < b.node;
 }
 
+__device__ __forceinline__ unsigned long long pq_key(float qs, float v) {
+    return (unsigned long long)__double_as_longlong(fabs((double)qs - (double)v));
+}
+
 __device__ __forceinline__ PQE pq_inf() {
     PQE e;
-    e.key = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+    e.key = 0x7ff0000000000000ull;  // +inf
     e.tree = 0x7fffffff;
     e.node = 0x7fffffff;
     return e;
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
                     const float qx = __ldg(q + nd.x);
                     const float qs = F.U ? reflect_coord(qx, w2, __ldg(F.U + (size_t)t * F.d + nd.x)) : qx;
                     const float v = __int_as_float(nd.y);
-                    e.key = fabs((double)qs - (double)v);
+                    e.key = pq_key(qs, v);
                     e.tree = t;
                     e.node = qs < v ? 2 * j + 2 : 2 * j + 1;  // the child not taken
                     j = qs < v ? 2 * j + 1 : 2 * j + 2;
@@ -143,27 +149,43 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
         while (checked < budget && head < cnt) {
             const PQE top = qa[head];
             ++head;
-            // lane 0 descends from the popped node, staging the siblings it passes
-            int nb = 0, leaf = 0;
-            if (lane == 0) {
-                int j = top.node;
-                const float w2 = F.U ? w2s[top.tree] : 0.f;
-                while (j < nn) {
-                    const int2 nd = __ldg(F.nodes + (size_t)top.tree * F.nnodes + j);
+            // descend from the popped node, staging the siblings passed.  The warp loads the
+            // five-level subtree below the current node at once (lane i: node i in breadth-first
+            // order, with its query coordinate), then walks it through shuffles: five levels cost
+            // one round of loads instead of five dependent ones.  Same path, same pushes.
+            const int tr = top.tree;
+            const int2 *tnodes = F.nodes + (size_t)tr * F.nnodes;
+            const float *u = F.U ? F.U + (size_t)tr * F.d : nullptr;
+            const float w2 = u ? w2s[tr] : 0.f;
+            const int lv = 31 - __clz(lane + 1);  // lane's level in the subtree (lanes 0..30)
+            int j = top.node, nb = 0;
+            while (j < nn) {
+                const long long node = (((long long)j + 1) << lv) - 1 + (lane + 1 - (1 << lv));
+                float qs_l = 0.f, v_l = 0.f;
+                if (lane < 31 && node < nn) {
+                    const int2 nd = __ldg(tnodes + node);
                     const float qx = __ldg(q + nd.x);
-                    const float qs = F.U ? reflect_coord(qx, w2, __ldg(F.U + (size_t)top.tree * F.d + nd.x)) : qx;
-                    const float v = __int_as_float(nd.y);
-                    PQE e;
-                    e.key = fabs((double)qs - (double)v);
-                    e.tree = top.tree;
-                    e.node = qs < v ? 2 * j + 2 : 2 * j + 1;
-                    j = qs < v ? 2 * j + 1 : 2 * j + 2;
-                    stage[nb++] = e;
+                    qs_l = u ? reflect_coord(qx, w2, __ldg(u + nd.x)) : qx;
+                    v_l = __int_as_float(nd.y);
                 }
-                leaf = j - nn;
-                out[checked] = leaf_code(top.tree, leaf, F.L);
+                int bi = 0;  // breadth-first index of the current node in the loaded subtree
+                for (int l = 0; l < 5 && j < nn; ++l) {
+                    const float qs = __shfl_sync(FULL, qs_l, bi);
+                    const float v = __shfl_sync(FULL, v_l, bi);
+                    const bool left = qs < v;
+                    if (lane == 0) {
+                        PQE e;
+                        e.key = pq_key(qs, v);
+                        e.tree = tr;
+                        e.node = left ? 2 * j + 2 : 2 * j + 1;
+                        stage[nb] = e;
+                    }
+                    ++nb;
+                    j = left ? 2 * j + 1 : 2 * j + 2;
+                    bi = left ? 2 * bi + 1 : 2 * bi + 2;
+                }
             }
-            nb = __shfl_sync(FULL, nb, 0);
+            if (lane == 0) out[checked] = leaf_code(tr, j - nn, F.L);
             __syncwarp();
             ++checked;
             // drop the popped prefix while merging; keep only what later pops can still take
