@@ -72,9 +72,10 @@ typedef struct gf_rand_params {
                             group of up to 16 queries and scored against all of them -- the bf16
                             screen on the tensor cores, float32 (direct form) on the CUDA cores;
                             per query the trees' lists are merged and de-duplicated by id, and the
-                            screen's R best reranked in float32.  bf16: R <= 32; float32: k <= 32;
-                            T * R <= 8192, T * 2^L <= 2^22; the workspace need not be zero and is
-                            left zero */
+                            screen's R best reranked in float32.  Runs the priority search too (the
+                            pairs are (query, leaf checked)); AUTO takes it for one leaf per tree
+                            only.  bf16: R <= 32; float32: k <= 32; (leaves per query) * R <= 8192,
+                            T * 2^L <= 2^22; the workspace need not be zero and is left zero */
 
 /* Order in which the streaming kernel's CTAs take the queries of a batch.  Results do not depend
  * on it; throughput does: queries that reach the same leaf of tree 0 share most candidates, and

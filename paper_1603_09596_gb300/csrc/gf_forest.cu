@@ -403,7 +403,7 @@ extern "C" int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_q
         x.leaf_budget = leaf_budget_of(F, o->checks, o->eps);
         x.ncand_out = o->ncand_out;
         const bool leaf_ok = gf_leaf_unsupported(F, m, 1, p, R, x) == nullptr;
-        const int64_t lb = gf_leaf_workspace_bytes(F, m, p, R, o->order);
+        const int64_t lb = gf_leaf_workspace_bytes(F, m, p, R, o->order, x.leaf_budget);
         if (o->algo == GF_ALGO_LEAF) *bytes = lb;
         else if (leaf_ok && gf_leaf_preferred(F, m, 1, p, R, x)) *bytes = std::max(*bytes, lb);
     }

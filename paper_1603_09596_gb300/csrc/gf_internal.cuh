@@ -137,11 +137,13 @@ inline int32_t leaf_budget_of(const gf_forest *F, int32_t checks, double eps) {
     return nl > F->T ? (int32_t)nl : 0;
 }
 
-// Leaf-major batched path (GF_ALGO_LEAF): one-leaf-per-tree queries, float32 or the bf16 screen.
+// Leaf-major batched path (GF_ALGO_LEAF): float32 or the bf16 screen.
+// leaf_budget > 0: the priority search's leaves (QueryExtra::leaf_budget), else one leaf per tree.
 int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision, int32_t R,
-                   int32_t order, cudaStream_t st, int64_t *ids, float *dists, void *workspace,
-                   int64_t workspace_bytes);
-int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order);
+                   int32_t order, int32_t leaf_budget, cudaStream_t st, int64_t *ids, float *dists,
+                   void *workspace, int64_t workspace_bytes);
+int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order,
+                                int32_t leaf_budget);
 // Whether GF_ALGO_AUTO takes the leaf-major path for this batch.
 bool gf_leaf_preferred(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R, const QueryExtra &x);
 // Why the leaf-major path cannot run this query (nullptr: it can).

@@ -3,12 +3,13 @@
 // cores (k_leaf_f32, further down), regrouped so that every leaf's points are read once per group
 // of queries that reach it.
 //
-// A query's candidates are the points of the T leaves it reaches (Eq. 1); its answer is the k
-// nearest of their union.  In a large batch many queries reach the same leaf of a tree (10^4
-// queries over 2^10 leaves: about ten each), and a per-query kernel reads that leaf's rows once per
-// query.  Here:
-//   1. descend: leaf[q][t] for every (query, tree);
-//   2. bucket the (query, tree) pairs by (tree, leaf) (counting sort);
+// A query's candidates are the points of the leaves it checks: one per tree (Eq. 1), or the leaves
+// of Alg. 2's shared priority queue (the first descent of every tree, then pops: slot t < T of a
+// query's list is tree t's first leaf); its answer is the k nearest of their union.  In a large
+// batch many queries check the same leaf (10^4 queries over 2^10 leaves per tree: about ten each),
+// and a per-query kernel reads that leaf's rows once per query.  Here:
+//   1. the leaves: leaf[q][t] by descent, or the priority search's list of S leaves per query;
+//   2. bucket the (query, slot) pairs by leaf (tree, leaf) (counting sort);
 //   3. cut every bucket into chunks of at most NQ queries and order the chunks: those of tree 0
 //      first, then the others by the smallest tree-0 leaf among their queries, so chunks of
 //      different trees that cover the same region of the data run at about the same time and find
@@ -22,15 +23,15 @@
 //      |x~ - q|^2 does (the two differ by |q|^2).  x~ is the bf16 copy of the forest; the query
 //      enters as two bf16 parts hi + lo (hi = bf16(q), lo = bf16(q - hi)), i.e. with about 16
 //      significant bits, so the screen is the distance to the bf16 points, as in the other kernels.
-//      Each (query, tree) keeps the R best (score, id) keys of its leaf that lie below the query's
+//      Each (query, slot) keeps the R best (score, id) keys of its leaf that lie below the query's
 //      bound tau_q, an upper bound on the R-th best key of the query's whole candidate union: the
 //      R-th best key of any of its leaves is one.  The chunks of tree 0 run first (a launch of
 //      their own) and set tau_q; every later chunk lowers it with its own R-th best (atomicMin).
 //      Nothing in the union's R best is lost: such a key lies below tau_q and among the R best of
 //      its leaf;
-//   5. merge (k_leaf_merge): per query the T lists are de-duplicated by id, the R best screened
-//      ids are rescored in float32 (direct form, the same code as the other kernels' rerank) and
-//      the k nearest are written in (distance, id) order.
+//   5. merge (k_leaf_merge): per query the keys of its S lists at or below its final bound are
+//      de-duplicated by id, the R best screened ids are rescored in float32 (direct form, the same
+//      code as the other kernels' rerank) and the k nearest are written in (distance, id) order.
 // Results are those of the screened search of the other kernels: the screen ranks the query's
 // candidate union, its R best are rescored exactly.  Screen scores near the shortlist boundary can
 // order differently from another kernel's screen (different float32 rounding), as between any two
@@ -279,12 +280,13 @@ struct LeafArgs {
     const int *item_hi;    // device: end of this launch's items
     const int *bcnt;       // queries per bucket
     const int *boff;       // first position of each bucket in qlist
-    const int *qlist;      // query ids grouped by bucket
+    const int *qlist;      // (query, slot) pairs q S + s grouped by bucket
     const __nv_bfloat16 *qhi, *qlo;  // [m][ldb] query parts (bf16 screen)
     const float *qf;                 // [m][ldx] the queries, rows padded (float32 kernel)
-    unsigned long long *part;        // [m][T][R] screened keys
+    unsigned long long *part;        // [m][S][R] keys of every (query, slot)
     unsigned long long *tau;         // [m] upper bound on each query's R-th best key
     int R;
+    int S;                           // slots (leaves) per query: T, or the priority search's budget
 };
 
 __device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A, int w, int &t, long long &lo,
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
 #pragma unroll
             for (int i = 0; i < NQ / 4; ++i) {
                 const int j = r0 + 4 * i;
-                qid[i] = j < nq ? A.qlist[q0pos + j] : -1;
+                qid[i] = j < nq ? A.qlist[q0pos + j] / A.S : -1;
             }
             const int nst = (rows + BM - 1) / BM * KC * SUB;  // the chunk's sub-tiles
             int ids[BM / 4];  // point ids of the lane's rows of tile `cur`
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
 #pragma unroll
             for (int j = 0; j < NQ; ++j) lst[j] = KEY_NONE;
             // lane j: query j of the chunk and its bound
-            const int my_qid = lane < nq ? A.qlist[q0pos + lane] : 0;
+            const int my_qid = lane < nq ? A.qlist[q0pos + lane] / A.S : 0;
             const unsigned long long my_tau = lane < nq ? __ldcg(A.tau + my_qid) : KEY_NONE;
             const int MT = (rows + BM - 1) / BM;
             for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
@@ -516,10 +518,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                 unsigned long long c = wl[(2 * NQ + j) * 32 + lane], d = wl[(3 * NQ + j) * 32 + lane];
                 if (lane >= RL) a = b = c = d = KEY_NONE;
                 const unsigned long long best = warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL);
-                const int qid = A.qlist[q0pos + j];
-                if (lane < R) A.part[((size_t)qid * F.T + t) * R + lane] = best;
+                const int pr = A.qlist[q0pos + j];  // q S + slot
+                if (lane < R) A.part[(size_t)pr * R + lane] = best;
                 const unsigned long long kth = __shfl_sync(FULL, best, R - 1);
-                if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + qid, kth);
+                if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + pr / A.S, kth);
             }
         }
     }
@@ -575,8 +577,8 @@ __global__ void __launch_bounds__(f32k::THREADS, f32k::CTAS_PER_SM) k_leaf_f32(F
         long long lo;
         chunk_of(F, A, w, t, lo, rows, q0pos, nq);
         const int ng = (nq + 3) >> 2;  // groups of four queries
-        const int qid_c = cr < nq ? A.qlist[q0pos + cr] : -1;
-        const int my_qid = lane < nq ? A.qlist[q0pos + lane] : 0;
+        const int qid_c = cr < nq ? A.qlist[q0pos + cr] / A.S : -1;
+        const int my_qid = lane < nq ? A.qlist[q0pos + lane] / A.S : 0;
         const unsigned long long my_tau = lane < nq ? __ldcg(A.tau + my_qid) : KEY_NONE;
         unsigned long long lst[NQ];
 #pragma unroll
@@ -680,10 +682,10 @@ __global__ void __launch_bounds__(f32k::THREADS, f32k::CTAS_PER_SM) k_leaf_f32(F
             unsigned long long c = wl[(2 * NQ + j) * 32 + lane], d = wl[(3 * NQ + j) * 32 + lane];
             if (lane >= RL) a = b = c = d = KEY_NONE;
             const unsigned long long best = warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL);
-            const int qid = A.qlist[q0pos + j];
-            if (lane < R) A.part[((size_t)qid * F.T + t) * R + lane] = best;
+            const int pr = A.qlist[q0pos + j];  // q S + slot
+            if (lane < R) A.part[(size_t)pr * R + lane] = best;
             const unsigned long long kth = __shfl_sync(FULL, best, R - 1);
-            if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + qid, kth);
+            if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + pr / A.S, kth);
         }
         __syncthreads();  // the lists are rewritten by the next chunk
     }
@@ -702,47 +704,66 @@ __global__ void k_qpad(const float *__restrict__ Q, long long m, int d, int ldx,
 
 // ---------------------------------------------------------------- batch regrouping
 
-__global__ void k_bucket_count(const int *__restrict__ leaf, long long pairs, int T, int L, int *bcnt) {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= pairs) return;
-    const int t = (int)(g % T);
-    atomicAdd(bcnt + ((size_t)t << L) + leaf[g], 1);
+// The bucket (leaf code tree << L | leaf) of pair g = q S + s, or -1 when the query checks fewer
+// than s + 1 leaves.  One leaf per tree: S = T and leaf[q T + t]; priority search: the list plist.
+__device__ __forceinline__ int pair_code(long long g, int S, int L, const int *leaf, const unsigned *plist,
+                                         const int *pn) {
+    const long long q = g / S;
+    const int sl = (int)(g - q * S);
+    if (plist) return sl < pn[q] ? (int)plist[g] : -1;
+    return (sl << L) + leaf[g];
 }
 
-__global__ void k_bucket_fill(const int *__restrict__ leaf, long long pairs, int T, int L,
-                              const int *__restrict__ boff, int *bfill, int *qlist) {
+// The leaf of tree 0 that query q reaches (slot 0 of either list).
+__device__ __forceinline__ int leaf0_of(long long q, int S, int L, const int *leaf, const unsigned *plist) {
+    return plist ? (int)(plist[q * S] & ((1u << L) - 1u)) : leaf[q * S];
+}
+
+struct PairSource {
+    const int *leaf;       // [m][T] (one leaf per tree) or null
+    const unsigned *plist; // [m][S] leaf codes in the order checked (priority search) or null
+    const int *pn;         // [m] leaves in each list
+    int S, L;
+};
+
+__global__ void k_pair_count(long long pairs, PairSource P, int *bcnt) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= pairs) return;
-    const int t = (int)(g % T);
-    const size_t u = ((size_t)t << L) + leaf[g];
-    qlist[boff[u] + atomicAdd(bfill + u, 1)] = (int)(g / T);
+    const int c = pair_code(g, P.S, P.L, P.leaf, P.plist, P.pn);
+    if (c >= 0) atomicAdd(bcnt + c, 1);
+}
+
+__global__ void k_pair_fill(long long pairs, PairSource P, const int *__restrict__ boff, int *bfill, int *qlist) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= pairs) return;
+    const int c = pair_code(g, P.S, P.L, P.leaf, P.plist, P.pn);
+    if (c >= 0) qlist[boff[c] + atomicAdd(bfill + c, 1)] = (int)g;
 }
 
 // Order key of a bucket (tree t = u >> L): in locality order 2^L * (t > 0) + the smallest tree-0
 // leaf among its queries, in tree-major order the bucket itself.  Either way the buckets of tree 0
 // take the keys below 2^L.
 __device__ __forceinline__ int bucket_key(int u, const int *bcnt, const int *boff, const int *qlist,
-                                          const int *leaf, int T, int L, bool locality) {
+                                          const PairSource &P, bool locality) {
     if (!locality) return u;
     int key = INT_MAX;
-    for (int i = 0; i < bcnt[u]; ++i) key = min(key, leaf[(size_t)qlist[boff[u] + i] * T]);
-    return ((u >> L) > 0 ? (1 << L) : 0) + key;
+    for (int i = 0; i < bcnt[u]; ++i) key = min(key, leaf0_of(qlist[boff[u] + i] / P.S, P.S, P.L, P.leaf, P.plist));
+    return ((u >> P.L) > 0 ? (1 << P.L) : 0) + key;
 }
 
 __global__ void k_item_count(int nb, const int *__restrict__ bcnt, const int *__restrict__ boff,
-                             const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int L, int locality,
-                             int *kcnt) {
+                             const int *__restrict__ qlist, PairSource P, int locality, int *kcnt) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nb || bcnt[u] == 0) return;
-    atomicAdd(kcnt + bucket_key(u, bcnt, boff, qlist, leaf, T, L, locality), (bcnt[u] + NQ - 1) / NQ);
+    atomicAdd(kcnt + bucket_key(u, bcnt, boff, qlist, P, locality), (bcnt[u] + NQ - 1) / NQ);
 }
 
 __global__ void k_item_fill(int nb, const int *__restrict__ bcnt, const int *__restrict__ boff,
-                            const int *__restrict__ qlist, const int *__restrict__ leaf, int T, int L, int locality,
+                            const int *__restrict__ qlist, PairSource P, int locality,
                             const int *__restrict__ koff, int *kfill, int2 *items) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nb || bcnt[u] == 0) return;
-    const int key = bucket_key(u, bcnt, boff, qlist, leaf, T, L, locality);
+    const int key = bucket_key(u, bcnt, boff, qlist, P, locality);
     const int n_it = (bcnt[u] + NQ - 1) / NQ;
     const int base = koff[key] + atomicAdd(kfill + key, n_it);
     for (int i = 0; i < n_it; ++i) items[base + i] = make_int2(u, i * NQ);
@@ -788,28 +809,42 @@ __global__ void k_qsplit(const float *__restrict__ Q, long long m, int d, int ld
 
 // ---------------------------------------------------------------- merge + rerank
 
-// Per query: the T lists of R keys -> distinct ids -> the R best -> (screened keys: float32
-// rerank) -> k nearest.  One CTA per query at a time.
+// Per query: the keys of its S lists of R at or below its final bound tau_q (every key of the
+// union's R best is) -> distinct ids -> the R best -> (screened keys: float32 rerank) -> k nearest.
+// One CTA per query at a time.
 template <int NCF>
 __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *__restrict__ Q, long long m, int k,
-                                                    int R, int rerank, const unsigned long long *__restrict__ part,
-                                                    long long *ids, float *dists) {
+                                                    int R, int S, int rerank,
+                                                    const unsigned long long *__restrict__ part,
+                                                    const unsigned long long *__restrict__ tau, long long *ids,
+                                                    float *dists) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TR = F.T * R;
-    int P = 2;
-    while (P < TR) P <<= 1;
+    const int TR = S * R;
+    int Pmax = 2;
+    while (Pmax < TR) Pmax <<= 1;
     unsigned long long *a = reinterpret_cast<unsigned long long *>(smem_raw);
-    unsigned long long *b = a + P;
-    float *qs = reinterpret_cast<float *>(b + P);
+    unsigned long long *b = a + Pmax;
+    float *qs = reinterpret_cast<float *>(b + Pmax);
     int *sid = reinterpret_cast<int *>(qs + ldq_of(F.d));
-    __shared__ int nshort;
+    __shared__ int nshort, nkeep;
     for (long long qi = blockIdx.x; qi < m; qi += gridDim.x) {
-        // (id, score) order brings the copies of an id together, its best score first
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            const unsigned long long key = i < TR ? part[qi * TR + i] : KEY_NONE;
-            a[i] = (key << 32) | (key >> 32);
+        const unsigned long long tq = tau[qi];
+        if (threadIdx.x == 0) {
+            nshort = 0;
+            nkeep = 0;
         }
-        if (threadIdx.x == 0) nshort = 0;
+        __syncthreads();
+        // the keys that can still be among the R best, as (id, score): the copies of an id
+        // come together, its best score first
+        for (int i = threadIdx.x; i < TR; i += blockDim.x) {
+            const unsigned long long key = part[qi * TR + i];
+            if (key != KEY_NONE && key <= tq) a[atomicAdd(&nkeep, 1)] = (key << 32) | (key >> 32);
+        }
+        __syncthreads();
+        const int n = nkeep;
+        int P = 2;
+        while (P < n) P <<= 1;
+        for (int i = n + threadIdx.x; i < P; i += blockDim.x) a[i] = KEY_NONE;
         block_sort<unsigned long long>(a, P);
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const unsigned long long v = a[i];
@@ -837,9 +872,9 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
     }
 }
 
-size_t merge_smem(const gf_forest *F, int R) {
+size_t merge_smem(const gf_forest *F, int S, int R) {
     int P = 2;
-    while (P < F->T * R) P <<= 1;
+    while (P < S * R) P <<= 1;
     return (size_t)2 * P * 8 + (size_t)ldq_of(F->d) * 4 + (size_t)R * 4;
 }
 
@@ -847,14 +882,15 @@ size_t merge_smem(const gf_forest *F, int R) {
 
 struct LeafWorkspace {
     size_t bcnt, bfill, kcnt, kfill, zero_end;  // counters, zeroed by every call
-    size_t boff, koff, leaf, qlist, items, qhi, qlo, part, tau, total;
+    size_t boff, koff, leaf, pn, qlist, items, qhi, qlo, part, tau, total;
 };
 
-LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int R, int order) {
+// S: leaves per query (T, or the priority search's budget)
+LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int S, int R, int order) {
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t nb = (size_t)F->T << F->L;
     const size_t nk = order == GF_ORDER_GIVEN ? nb : ((size_t)2 << F->L);
-    const size_t pairs = (size_t)m * F->T;
+    const size_t pairs = (size_t)m * S;
     LeafWorkspace W;
     size_t o = 0;
     W.bcnt = o; o = al(o + nb * 4);
@@ -864,7 +900,8 @@ LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int R, int order) {
     W.zero_end = o;
     W.boff = o; o = al(o + (nb + 1) * 4);
     W.koff = o; o = al(o + (nk + 1) * 4);
-    W.leaf = o; o = al(o + pairs * 4);
+    W.leaf = o; o = al(o + pairs * 4);  // leaf[m][T] or the priority lists [m][S]
+    W.pn = o; o = al(o + (size_t)m * 4);
     W.qlist = o; o = al(o + pairs * 4);
     W.items = o; o = al(o + pairs * 8);
     W.qhi = o; o = al(o + (size_t)m * F->ldb * 2);
@@ -883,40 +920,50 @@ const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_
                                 const QueryExtra &x) {
     if (precision != GF_BF16_RERANK && precision != GF_FP32) return "the leaf-major path runs float32 or the bf16 screen";
     if (precision == GF_BF16_RERANK && (!F->xb || !F->xbn)) return "the forest has no bf16 copy";
-    if (x.leaf_budget > 0) return "the leaf-major path runs the one-leaf-per-tree search only";
     if (x.ncand_out) return "candidate counts are reported by the streaming kernel only";
+    const int S = x.leaf_budget > 0 ? x.leaf_budget : F->T;  // leaves per query
+    if (x.leaf_budget > 0 && ((unsigned long long)F->T << F->L) > 0xffffffffull)
+        return "the priority search needs T * 2^L <= 2^32";
     if (precision == GF_FP32) {
-        if (k > R_MAX) return "the leaf-major float32 path keeps at most 32 per (query, tree): k <= 32";
+        if (k > R_MAX) return "the leaf-major float32 path keeps at most 32 per (query, leaf): k <= 32";
         R = k;
     }
     if (R < 1 || R > R_MAX) return "the leaf-major path keeps a shortlist of 1..32";
     if (k > R) return "k exceeds the shortlist";
-    if ((int64_t)F->T * R > MAX_KEYS) return "T * R above 8192";
+    if ((int64_t)S * R > MAX_KEYS) return "(leaves per query) * R above 8192";
     if (((int64_t)F->T << F->L) > ((int64_t)1 << 22)) return "T * 2^L above 2^22 buckets";
-    if (m * F->T > INT_MAX / 2) return "m * T above 2^30";
+    if (m * S > INT_MAX / 2) return "m * (leaves per query) above 2^30";
     return nullptr;
 }
 
 // The regrouping pays once leaves are shared: on average at least LEAF_MIN_SHARE queries per leaf.
 constexpr int LEAF_MIN_SHARE = 4;
 
+// The priority search is left to the streaming kernel: its leaves are small (the paper's p of a
+// few dozen points), a chunk fills part of a row tile, and per-chunk costs dominate (at 10^6 x 960,
+// p = 64, c = 512: 57.7 ms against 45.6 ms per 10^4 queries, bf16).  GF_ALGO_LEAF still runs it.
 bool gf_leaf_preferred(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R, const QueryExtra &x) {
-    return gf_leaf_unsupported(F, m, k, precision, R, x) == nullptr && (m >> F->L) >= LEAF_MIN_SHARE;
+    return x.leaf_budget == 0 && gf_leaf_unsupported(F, m, k, precision, R, x) == nullptr &&
+           (m >> F->L) >= LEAF_MIN_SHARE;
 }
 
-int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order) {
-    // float32 keeps k <= 32 per (query, tree): size for the most
+int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order,
+                                int32_t leaf_budget) {
+    // float32 keeps k <= 32 per (query, leaf): size for the most
     const int len = precision == GF_FP32 ? R_MAX : std::max(1, std::min(R, R_MAX));
-    return (int64_t)leaf_workspace(F, m, len, order_of(order)).total;
+    const int S = leaf_budget > 0 ? leaf_budget : F->T;
+    return (int64_t)leaf_workspace(F, m, S, len, order_of(order)).total;
 }
 
 int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision, int32_t R,
-                   int32_t order, cudaStream_t st, int64_t *ids, float *dists, void *workspace,
-                   int64_t workspace_bytes) {
+                   int32_t order, int32_t leaf_budget, cudaStream_t st, int64_t *ids, float *dists,
+                   void *workspace, int64_t workspace_bytes) {
     order = order_of(order);
     const bool f32 = precision == GF_FP32;
-    if (f32) R = k;  // the exact distances: the k best of every (query, tree) suffice
-    const LeafWorkspace W = leaf_workspace(F, m, R, order);
+    if (f32) R = k;  // the exact distances: the k best of every (query, leaf) suffice
+    const bool prio = leaf_budget > 0;  // Alg. 2's priority search: a list of S leaves per query
+    const int S = prio ? leaf_budget : F->T;
+    const LeafWorkspace W = leaf_workspace(F, m, S, R, order);
     char *ws = (char *)workspace;
     bool own = false;
     if (ws) {
@@ -937,31 +984,38 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     int *bcnt = (int *)(ws + W.bcnt), *bfill = (int *)(ws + W.bfill);
     int *kcnt = (int *)(ws + W.kcnt), *kfill = (int *)(ws + W.kfill);
     int *boff = (int *)(ws + W.boff), *koff = (int *)(ws + W.koff);
-    int *leaf = (int *)(ws + W.leaf), *qlist = (int *)(ws + W.qlist);
+    int *leaf = (int *)(ws + W.leaf), *pn = (int *)(ws + W.pn), *qlist = (int *)(ws + W.qlist);
     int2 *items = (int2 *)(ws + W.items);
     __nv_bfloat16 *qhi = (__nv_bfloat16 *)(ws + W.qhi), *qlo = (__nv_bfloat16 *)(ws + W.qlo);
     unsigned long long *part = (unsigned long long *)(ws + W.part);
     unsigned long long *tau = (unsigned long long *)(ws + W.tau);
     const int nb = F->T << F->L;
     const int nk = order == GF_ORDER_GIVEN ? nb : (2 << F->L);
-    const long long pairs = (long long)m * F->T;
+    const long long pairs = (long long)m * S;
     const bool locality = order != GF_ORDER_GIVEN;
 
     cudaError_t e = cudaMemsetAsync(ws, 0, W.zero_end, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(tau, 0xff, (size_t)m * 8, st);  // KEY_NONE: no bound yet
     if (e != cudaSuccess) return fail(e, "workspace memset");
-    int r = gf_descend(F, Q, m, leaf, st);
+    // the leaves of every query: the descents, or the priority search's lists
+    int r = prio ? gf_launch_prio_leaves(F, Q, m, S, (unsigned *)leaf, pn, st) : gf_descend(F, Q, m, leaf, st);
     if (r) {
         if (own) cudaFreeAsync(ws, st);
         return r;
     }
+    PairSource P;
+    P.leaf = prio ? nullptr : leaf;
+    P.plist = prio ? (const unsigned *)leaf : nullptr;
+    P.pn = pn;
+    P.S = S;
+    P.L = F->L;
     const unsigned pg = (unsigned)((pairs + 255) / 256), bg = (unsigned)((nb + 255) / 256);
-    k_bucket_count<<<pg, 256, 0, st>>>(leaf, pairs, F->T, F->L, bcnt);
+    k_pair_count<<<pg, 256, 0, st>>>(pairs, P, bcnt);
     k_scan<<<1, 1024, 0, st>>>(bcnt, nb, boff);
-    k_bucket_fill<<<pg, 256, 0, st>>>(leaf, pairs, F->T, F->L, boff, bfill, qlist);
-    k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, F->L, locality, kcnt);
+    k_pair_fill<<<pg, 256, 0, st>>>(pairs, P, boff, bfill, qlist);
+    k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, P, locality, kcnt);
     k_scan<<<1, 1024, 0, st>>>(kcnt, nk, koff);
-    k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, leaf, F->T, F->L, locality, koff, kfill, items);
+    k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, P, locality, koff, kfill, items);
     // float32: the padded query copy takes the place of the two bf16 parts (as large together)
     float *qf = (float *)(ws + W.qhi);
     if (f32) k_qpad<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldx, qf);
@@ -982,6 +1036,7 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     A.part = part;
     A.tau = tau;
     A.R = R;
+    A.S = S;
     // the chunks of tree 0 (keys below 2^L) set every query's bound; then all the others
     for (int wave = 0; wave < 2; ++wave) {
         A.item_lo = wave == 0 ? koff : koff + (1 << F->L);
@@ -991,7 +1046,7 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major scoring launch");
 
-    const size_t msmem = merge_smem(F, R);
+    const size_t msmem = merge_smem(F, S, R);
     const unsigned mg = (unsigned)std::min<long long>(m, (long long)F->num_sms * 16);
     const int ncf = F->ldx / 4 <= 32 ? 1 : F->ldx / 4 <= 64 ? 2 : F->ldx / 4 <= 128 ? 4 : F->ldx / 4 <= 256 ? 8 : 0;
 #define GF_MERGE(NCV)                                                                                    \
@@ -1000,7 +1055,7 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
             (e = cudaFuncSetAttribute(k_leaf_merge<NCV>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                       (int)msmem)) != cudaSuccess)                                       \
             return fail(e, "cudaFuncSetAttribute(k_leaf_merge)");                                        \
-        k_leaf_merge<NCV><<<mg, 128, msmem, st>>>(view_of(F), Q, m, k, R, !f32, part, (long long *)ids, dists); \
+        k_leaf_merge<NCV><<<mg, 128, msmem, st>>>(view_of(F), Q, m, k, R, S, !f32, part, tau, (long long *)ids, dists); \
     }
     GF_MERGE(1) GF_MERGE(2) GF_MERGE(4) GF_MERGE(8) GF_MERGE(0)
 #undef GF_MERGE

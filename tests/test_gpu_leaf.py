@@ -184,6 +184,59 @@ def test_leaf_fp32_agrees_with_streaming(gf):
                       b[1].cpu().numpy().astype(np.float64))
 
 
+def priority_candidates(F, seq, nl):
+    """Sorted distinct point ids of the leaves each query checked (the oracle's leaf sequence)."""
+    offs, ids = [0], []
+    for i in range(seq.shape[0]):
+        pts = set()
+        for code in seq[i, :nl[i]]:
+            t, b = int(code) >> F.L, int(code) & ((1 << F.L) - 1)
+            lo, hi = (b * F.n) >> F.L, ((b + 1) * F.n) >> F.L
+            pts.update(F.perm[t, lo:hi].tolist())
+        ids.extend(sorted(pts))
+        offs.append(len(ids))
+    return np.asarray(offs, dtype=np.int64), np.asarray(ids, dtype=np.int64)
+
+
+# Alg. 2 with the shared priority queue through the leaf-major path: each query's list of leaves
+# from the priority kernel, the (query, slot) pairs grouped by leaf
+PRIO_CASES = [("tiny", 24), ("shared", 20), ("gist_like", 48), ("crowded", 9)]
+
+
+@pytest.mark.parametrize("name,c", PRIO_CASES)
+def test_leaf_priority_fp32_matches_oracle(gf, name, c):
+    X, Q, F = case(name)
+    G = gpu_forest(gf, X, F)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, checks=c, algo=gf.GF_ALGO_LEAF)
+    oi, od, _, _ = oracle.search_priority(F, X, Q, 10, c)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+    assert gf.gf_kernel_status() == 0
+
+
+@pytest.mark.parametrize("name,c", PRIO_CASES)
+def test_leaf_priority_bf16_matches_oracle(gf, name, c):
+    X, Q, F = case(name)
+    G = gpu_forest(gf, X, F)
+    R = 16
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, precision=gf.GF_BF16_RERANK, rerank_R=R,
+                         checks=c, algo=gf.GF_ALGO_LEAF)
+    _, _, _, nl, seq = oracle.search_priority(F, X, Q, 10, c, return_leaves=True)
+    offs, ids = priority_candidates(F, seq, nl)
+    oi, od, _ = screen.screened_search(F, X, Q, 10, R, "bf16", offs, ids)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+
+
+def test_leaf_priority_agrees_with_streaming(gf):
+    # the same priority search, float32, by the streaming kernel and the leaf-major path
+    X, Q, F = case("shared")
+    G = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    a = gf.gf_query(G, Qg, 10, checks=20, algo=gf.GF_ALGO_LEAF)
+    b = gf.gf_query(G, Qg, 10, checks=20, algo=gf.GF_ALGO_STREAM)
+    assert_topk_close(X, Q, a[0].cpu().numpy(), a[1].cpu().numpy(), b[0].cpu().numpy(),
+                      b[1].cpu().numpy().astype(np.float64))
+
+
 def test_leaf_rejects_what_it_does_not_run(gf):
     X, Q, F = case("tiny")
     G = gpu_forest(gf, X, F)
@@ -191,7 +244,7 @@ def test_leaf_rejects_what_it_does_not_run(gf):
     Qg = torch.from_numpy(Q).cuda()
     for kw in (dict(precision=gf.GF_FP8_RERANK),                             # the fp8 screen
                dict(precision=gf.GF_BF16_RERANK, rerank_R=33),               # shortlist above 32
-               dict(precision=gf.GF_BF16_RERANK, rerank_R=16, checks=64)):  # priority search
+               dict(precision=gf.GF_BF16_RERANK, rerank_R=16, checks=1024)):  # 1024 leaves x R > 8192
         with pytest.raises(gf.GFError) as e:
             gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_LEAF, **kw)
         assert e.value.code == gf.GF_EUNSUPPORTED
