@@ -150,3 +150,34 @@ def test_full_size_high_d(gf):
     idx = np.sort(rng.choice(m, 60, replace=False))
     check_sampled_queries(gf, G, F, X, Q, k, idx, precisions=("fp32", "bf16", "fp8"))
     G.free()
+
+
+def test_full_size_leaf_major_batch(gf):
+    # the headline launch: the whole 10^4-query batch through the leaf-major path (bf16 screen with
+    # R = 16, and float32), sampled rows checked against the oracle on the same GPU-built forest
+    n, d, m, T, p, law, k = FULL["gist1m_p1024"]
+    X, Q = data("gist1m_p1024")
+    G, F = gpu_forest(gf, "gist1m_p1024")
+    gf.gf_forest_add_screen(G, gf.GF_BF16_RERANK)
+    Qg = torch.from_numpy(Q).cuda()
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(m, 200, replace=False))
+    Qs = Q[idx]
+    offs, ids = oracle.candidates(F, oracle.descend(F, Qs))
+    cs = candidate_sets(offs, ids)
+    # float32
+    gi, gd = gf.gf_query(G, Qg, k, algo=gf.GF_ALGO_LEAF)
+    oi, od = oracle.topk(X, Qs, offs, ids, k)
+    assert_topk_close(X, Qs, gi.cpu().numpy()[idx], gd.cpu().numpy()[idx], oi, od, cs)
+    # bf16 screen, R = 16
+    gi, gd = gf.gf_query(G, Qg, k, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_LEAF)
+    gi, gd = gi.cpu().numpy()[idx], gd.cpu().numpy()[idx]
+    si, sd, _ = screen.screened_search(F, X, Qs, k, 16, "bf16", offs, ids)
+    same = (gi == si).all(axis=1)
+    assert same.mean() >= 0.97, f"{same.mean():.3f} of rows agree"
+    for i in range(len(idx)):
+        for gid, dist in zip(gi[i], gd[i]):
+            assert gid in cs[i]
+            assert abs(oracle.dist2(Qs[i], X[gid]) - dist) <= 1e-5 * dist
+    assert gf.gf_kernel_status() == 0
+    G.free()
