@@ -80,14 +80,30 @@ def test_leaf_matches_oracle(gf, name, R):
     assert gf.gf_kernel_status() == 0
 
 
-@pytest.mark.parametrize("k", [1, 5])
-def test_leaf_small_k(gf, k):
+@pytest.mark.parametrize("k,R", [(1, 1), (1, 16), (5, 16), (7, 7)])
+def test_leaf_small_k(gf, k, R):
+    # shortlists shorter than a power of two and of length one
     X, Q, F = case("shared")
     G = gpu_forest(gf, X, F)
-    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.GF_BF16_RERANK, rerank_R=16,
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.GF_BF16_RERANK, rerank_R=R,
                          algo=gf.GF_ALGO_LEAF)
-    oi, od, cands = oracle_screen(F, X, Q, k, 16)
+    oi, od, cands = oracle_screen(F, X, Q, k, R)
     assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+
+
+@pytest.mark.parametrize("m", [1, 33])
+def test_leaf_tiny_batches(gf, m):
+    # a batch of one query, and one that does not fill a chunk
+    X, Q, F = case("tiny")
+    G = gpu_forest(gf, X, F)
+    Qs = np.ascontiguousarray(Q[:m])
+    gi, gd = gf.gf_query(G, torch.from_numpy(Qs).cuda(), 10, precision=gf.GF_BF16_RERANK, rerank_R=16,
+                         algo=gf.GF_ALGO_LEAF)
+    oi, od, cands = oracle_screen(F, X, Qs, 10, 16)
+    assert_screened_close(X, Qs, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+    fi, fd = gf.gf_query(G, torch.from_numpy(Qs).cuda(), 10, algo=gf.GF_ALGO_LEAF)
+    oi, od = oracle.search(F, X, Qs, 10)
+    assert_topk_close(X, Qs, fi.cpu().numpy(), fd.cpu().numpy(), oi, od)
 
 
 def test_leaf_full_shortlist_equals_fp32(gf):
@@ -133,6 +149,39 @@ def test_leaf_caller_workspace_is_left_zero(gf):
     s = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_STREAM, workspace=ws2)
     t = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=16, algo=gf.GF_ALGO_STREAM)
     assert torch.equal(s[0], t[0]) and torch.equal(s[1], t[1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_leaf_in_a_cuda_graph(gf, prec):
+    # the benchmark's launch: captured once with a caller workspace (nothing allocates inside the
+    # capture), replayed; the replays equal a direct call
+    X, Q, F = case("shared")
+    G = gpu_forest(gf, X, F)
+    p = gf.PRECISIONS[prec]
+    Qg = torch.from_numpy(Q).cuda()
+    m, k = Q.shape[0], 10
+    ws = torch.zeros(gf.gf_query_workspace_size(G, m, precision=p, rerank_R=16, algo=gf.GF_ALGO_LEAF),
+                     dtype=torch.uint8, device="cuda")
+    ids = torch.empty((m, k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    kw = dict(precision=p, rerank_R=16, algo=gf.GF_ALGO_LEAF, workspace=ws, stream=s, out=(ids, dd))
+    with torch.cuda.stream(s):
+        gf.gf_query(G, Qg, k, **kw)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        gf.gf_query(G, Qg, k, **kw)
+    ref = gf.gf_query(G, Qg, k, precision=p, rerank_R=16, algo=gf.GF_ALGO_LEAF)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        ids.fill_(-7)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(ids, ref[0]) and torch.equal(dd, ref[1])
+    assert int(ws.count_nonzero()) == 0
 
 
 def test_leaf_agrees_with_streaming_screen(gf):
