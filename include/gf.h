@@ -183,6 +183,32 @@ int gf_forest_export(const gf_forest *F, int32_t *split_dim_host, float *split_v
 int gf_forest_get_info(const gf_forest *F, gf_forest_info *info);
 
 /*
+ * gf_forest_save -- write the forest to a file: its points, the split of every node and the leaf
+ * order of every tree (Alg. 1's output), its Householder vectors (Sec. 2.2) if any, which
+ * screening copies it holds and its tuning.  The file is written next to `path` and renamed onto
+ * it once complete, so an existing file is replaced whole or not at all.
+ * Layout (little-endian): a 128-byte header -- "GFFOREST", u32 version 1, u32 0x01020304, i64 n,
+ * i32 d, T, leaf_size, L, u32 flags (1 reflections, 2 bf16 screen, 4 fp8 screen), i32 tuning
+ * warps[3] ctas[3] rerank_R[3] rows_in_flight[3], u32 0, u64 payload bytes, u64 s1, u64 s2,
+ * u64 0 -- then nodes [T][2^L - 1] x (i32 dim, f32 value), perm [T][n] i32, U [T][d] f32 (flag 1
+ * only), X [n][d] f32.  s1 = sum w_i and s2 = sum (i + 1) w_i (mod 2^64) over the payload's u32
+ * words w_0, w_1, ...
+ * Errors: GF_EINVAL (null forest or empty path), GF_EIO (the file cannot be created or written;
+ * no partial file is left), GF_ENOMEM, GF_ECUDA.  Synchronous.
+ */
+int gf_forest_save(const gf_forest *F, const char *path);
+
+/*
+ * gf_forest_load -- read a file written by gf_forest_save (or by any writer of the same layout)
+ * into a new forest that answers every query exactly as the saved one did; screening copies are
+ * derived again from X.  The whole file is read and checked on the host before the device is
+ * touched.  Errors: GF_EINVAL (null argument), GF_EIO (missing or unreadable file, bad magic,
+ * version, header or sizes, truncated or trailing bytes, checksum mismatch, a split dimension or
+ * leaf order that is not valid, NaN/Inf in X or U), GF_ENOMEM, GF_ECUDA.  Synchronous.
+ */
+int gf_forest_load(const char *path, gf_forest **out);
+
+/*
  * gf_forest_add_screen -- derive the low-precision copy of the points used by a screened
  * precision (Sec. 3 "Distance computation": ranking cost is the distance evaluation).
  *   GF_BF16_RERANK: xb[i][j] = bf16_rne(X[i][j])

@@ -638,11 +638,6 @@ struct DevBuf {
 
 }  // namespace
 
-int gf_forest_alloc(gf_forest **out, const float *X, int64_t n, int32_t d, int32_t T,
-                    int32_t leaf_size, bool borrow, cudaStream_t st);
-void gf_forest_destroy(gf_forest *F);
-int gf_check_finite(const float *X, int64_t count, cudaStream_t st);
-
 static int build_levels(gf_forest *F, const gf_rand_params &rp, uint64_t seed, cudaStream_t st) {
     const long long n = F->n;
     const int T = F->T, L = F->L;
@@ -739,8 +734,6 @@ static int build_levels(gf_forest *F, const gf_rand_params &rp, uint64_t seed, c
     GF_CUDA_TRY(cudaStreamSynchronize(st));
     return GF_OK;
 }
-
-int gf_forest_set_U(gf_forest *F, const float *U_host);
 
 static int build_any(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size, const gf_rand_params *rp_in,
                      uint64_t seed, const float *U_host, int32_t borrow_x, void *stream, gf_forest **out);

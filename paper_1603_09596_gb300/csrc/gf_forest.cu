@@ -74,7 +74,8 @@ static void forest_release(gf_forest *F) {
     delete F;
 }
 
-// Shape fields and the storage of x / nodes / perm.  borrow: keep X itself.
+// Shape fields and the storage of x / nodes / perm.  borrow: keep X itself.  X may be a device or
+// a host pointer when it is copied (the copies infer the direction from the address).
 int gf_forest_alloc(gf_forest **out, const float *X, int64_t n, int32_t d, int32_t T,
                     int32_t leaf_size, bool borrow, cudaStream_t st) {
     *out = nullptr;
@@ -112,10 +113,10 @@ int gf_forest_alloc(gf_forest **out, const float *X, int64_t n, int32_t d, int32
             cudaError_t e = cudaMemsetAsync(F->x, 0, (size_t)n * F->ldx * 4, st);
             if (e == cudaSuccess)
                 e = cudaMemcpy2DAsync(F->x, (size_t)F->ldx * 4, X, (size_t)d * 4, (size_t)d * 4, (size_t)n,
-                                      cudaMemcpyDeviceToDevice, st);
+                                      cudaMemcpyDefault, st);
             if (e != cudaSuccess) { forest_release(F); return gf_cuda_fail(e, "copy X"); }
         } else {
-            cudaError_t e = cudaMemcpyAsync(F->x, X, (size_t)n * d * 4, cudaMemcpyDeviceToDevice, st);
+            cudaError_t e = cudaMemcpyAsync(F->x, X, (size_t)n * d * 4, cudaMemcpyDefault, st);
             if (e != cudaSuccess) { forest_release(F); return gf_cuda_fail(e, "copy X"); }
         }
     }
@@ -158,23 +159,17 @@ int gf_check_finite(const float *X, int64_t count, cudaStream_t st) {
 
 // ---------------------------------------------------------------- import / export
 
-extern "C" int gf_forest_import(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
-                                const int32_t *split_dim_host, const float *split_val_host,
-                                const int32_t *perm_host, gf_forest **out) {
-    if (!out) return gf_fail(GF_EINVAL, "out is null");
-    *out = nullptr;
-    if (!split_dim_host || !split_val_host || !perm_host) return gf_fail(GF_EINVAL, "null host array");
-    gf_forest *F = nullptr;
-    cudaStream_t st = 0;
-    int r = gf_forest_alloc(&F, X, n, d, T, leaf_size, false, st);
-    if (r) return r;
+// Validate a host tree structure and copy it into F (nodes, perm), then check X for NaN/Inf.
+// On error F is left for the caller to release.
+int gf_forest_fill_structure(gf_forest *F, const int32_t *split_dim_host, const float *split_val_host,
+                             const int32_t *perm_host) {
+    const int64_t n = F->n;
+    const int32_t d = F->d, T = F->T;
     const size_t nn = ((size_t)1 << F->L) - 1;
     std::vector<int2> nodes((size_t)T * nn);
     for (size_t i = 0; i < nodes.size(); ++i) {
-        if (split_dim_host[i] < 0 || split_dim_host[i] >= d) {
-            forest_release(F);
+        if (split_dim_host[i] < 0 || split_dim_host[i] >= d)
             return gf_fail(GF_EINVAL, "split_dim[%zu] = %d outside [0, %d)", i, split_dim_host[i], d);
-        }
         int32_t bits;
         std::memcpy(&bits, &split_val_host[i], 4);
         nodes[i] = make_int2(split_dim_host[i], bits);
@@ -184,18 +179,31 @@ extern "C" int gf_forest_import(const float *X, int64_t n, int32_t d, int32_t T,
         std::fill(seen.begin(), seen.end(), 0);
         for (int64_t i = 0; i < n; ++i) {
             const int32_t v = perm_host[(size_t)t * n + i];
-            if (v < 0 || v >= n || seen[v]) {
-                forest_release(F);
+            if (v < 0 || v >= n || seen[v])
                 return gf_fail(GF_EINVAL, "perm row %d is not a permutation of 0..n-1", t);
-            }
             seen[v] = 1;
         }
     }
     cudaError_t e = cudaMemcpy(F->nodes, nodes.data(), nodes.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(F->perm, perm_host, (size_t)T * n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) { forest_release(F); return gf_cuda_fail(e, "import copy"); }
-    if ((r = gf_check_finite(F->x, (int64_t)n * F->ldx, st))) { forest_release(F); return r; }
+    if (e != cudaSuccess) return gf_cuda_fail(e, "import copy");
+    return gf_check_finite(F->x, (int64_t)n * F->ldx, 0);
+}
+
+extern "C" int gf_forest_import(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
+                                const int32_t *split_dim_host, const float *split_val_host,
+                                const int32_t *perm_host, gf_forest **out) {
+    if (!out) return gf_fail(GF_EINVAL, "out is null");
+    *out = nullptr;
+    if (!split_dim_host || !split_val_host || !perm_host) return gf_fail(GF_EINVAL, "null host array");
+    gf_forest *F = nullptr;
+    int r = gf_forest_alloc(&F, X, n, d, T, leaf_size, false, 0);
+    if (r) return r;
+    if ((r = gf_forest_fill_structure(F, split_dim_host, split_val_host, perm_host))) {
+        forest_release(F);
+        return r;
+    }
     *out = F;
     return GF_OK;
 }

@@ -112,6 +112,18 @@ int gf_cuda_fail(cudaError_t e, const char *what);
 int gf_dmalloc(void **p, size_t bytes);
 
 // ---------------------------------------------------------------- entry points between units
+
+// Forest storage (gf_forest.cu).  gf_forest_alloc: shape fields and storage of x / nodes / perm;
+// X is copied (from a device or host address) unless borrow.  gf_forest_fill_structure: validate
+// a host tree structure, upload it and check X for NaN/Inf (on error the caller releases F).
+int gf_forest_alloc(gf_forest **out, const float *X, int64_t n, int32_t d, int32_t T,
+                    int32_t leaf_size, bool borrow, cudaStream_t st);
+void gf_forest_destroy(gf_forest *F);
+int gf_check_finite(const float *X, int64_t count, cudaStream_t st);
+int gf_forest_fill_structure(gf_forest *F, const int32_t *split_dim_host, const float *split_val_host,
+                             const int32_t *perm_host);
+int gf_forest_set_U(gf_forest *F, const float *U_host);
+
 struct QueryExtra {
     int32_t algo = GF_ALGO_AUTO;
     void *workspace = nullptr;

@@ -82,6 +82,8 @@ def lib() -> C.CDLL:
             "gf_forest_import": ([P, i64, i32, i32, i32, P, P, P, P], i32),
             "gf_forest_export": ([P, P, P, P], i32),
             "gf_forest_get_info": ([P, P], i32),
+            "gf_forest_save": ([P, C.c_char_p], i32),
+            "gf_forest_load": ([C.c_char_p, P], i32),
             "gf_forest_add_screen": ([P, i32, P], i32),
             "gf_forest_set_tuning": ([P, i32, i32, i32, i32, i32], i32),
             "gf_forest_free": ([P], i32),
@@ -221,6 +223,16 @@ def gf_forest_export(F: Forest):
     pm = np.empty((inf.T, inf.n), dtype=np.int32)
     _check(lib().gf_forest_export(F.handle, sd.ctypes.data, sv.ctypes.data, pm.ctypes.data))
     return sd, sv, pm
+
+
+def gf_forest_save(F: Forest, path) -> None:
+    _check(lib().gf_forest_save(F.handle, os.fsencode(path)))
+
+
+def gf_forest_load(path) -> Forest:
+    h = C.c_void_p()
+    _check(lib().gf_forest_load(os.fsencode(path), C.byref(h)))
+    return Forest(h)
 
 
 def gf_forest_add_screen(F: Forest, precision: int, stream=None) -> None:
