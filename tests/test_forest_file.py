@@ -209,7 +209,7 @@ def test_save_load_round_trip(gf, tmp_path):
     Xg, Qg = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
     G = gf.gf_build(Xg, T, 64, seed=11, U=U)
     gf.gf_forest_add_screen(G, gf.GF_BF16_RERANK)
-    gf.gf_forest_set_tuning(G, gf.GF_BF16_RERANK, 4, 2, 48, 2)
+    gf.gf_forest_set_tuning(G, gf.GF_BF16_RERANK, 4, 2, 24, 2)
     path = tmp_path / "f.gff"
     gf.gf_forest_save(G, path)
     assert not os.path.exists(str(path) + ".tmp")
@@ -222,13 +222,13 @@ def test_save_load_round_trip(gf, tmp_path):
     assert f["flags"] == 1 | 2
     assert np.array_equal(f["split_dim"], sd) and np.array_equal(f["split_val"].view(np.int32), sv.view(np.int32))
     assert np.array_equal(f["perm"], pm) and np.array_equal(f["X"], X) and np.array_equal(f["U"], U)
-    assert list(f["tuning"][:, gf.GF_BF16_RERANK]) == [4, 2, 48, 2]
+    assert list(f["tuning"][:, gf.GF_BF16_RERANK]) == [4, 2, 24, 2]
 
     H = gf.gf_forest_load(path)
     _same_structure(gf, G, H)
     hi = H.info
     assert hi.screens == inf.screens and hi.device_bytes == inf.device_bytes
-    # every path answers bit for bit as before: the tuned shortlist (R = 48) comes back too
+    # every path answers bit for bit as before: the tuned shortlist (R = 24) comes back too
     for kw in (dict(), dict(precision=gf.GF_BF16_RERANK, algo=gf.GF_ALGO_LEAF),
                dict(precision=gf.GF_BF16_RERANK, algo=gf.GF_ALGO_STREAM), dict(checks=24),
                dict(precision=gf.GF_BF16_RERANK, checks=24, algo=gf.GF_ALGO_LEAF)):
