@@ -119,7 +119,8 @@ int save_impl(const gf_forest *F, const std::string &path) {
     std::vector<int32_t> perm(T * n);
     std::vector<float> U(F->U ? T * d : 0);
     GF_CUDA_TRY(cudaDeviceSynchronize());
-    GF_CUDA_TRY(cudaMemcpy(nodes.data(), F->nodes, nodes.size() * sizeof(int2), cudaMemcpyDeviceToHost));
+    if (!nodes.empty())  // a single-leaf forest (L = 0) has no internal node
+        GF_CUDA_TRY(cudaMemcpy(nodes.data(), F->nodes, nodes.size() * sizeof(int2), cudaMemcpyDeviceToHost));
     GF_CUDA_TRY(cudaMemcpy(perm.data(), F->perm, perm.size() * 4, cudaMemcpyDeviceToHost));
     if (F->U) GF_CUDA_TRY(cudaMemcpy(U.data(), F->U, U.size() * 4, cudaMemcpyDeviceToHost));
     // X leaves the device in slabs of about 64 MB (rows unpadded: the file holds d floats a row).

@@ -295,3 +295,22 @@ def test_save_failures_leave_no_file(gf, small, tmp_path):
     gf.gf_forest_save(G, p)
     H = gf.gf_forest_load(p)
     _same_structure(gf, G, H)
+
+
+@pytest.mark.gpu
+def test_single_leaf_forest_round_trip(gf, tmp_path):
+    """leaf_size >= n: no internal node (L = 0), every query scans all points; the file still
+    round-trips and the loaded forest is exact."""
+    X, Q = synth.mixture(500, 24, 20, "A", seed=2, qseed=3)
+    G = gf.gf_build(torch.from_numpy(X).cuda(), 3, 500, seed=1)
+    assert G.info.L == 0
+    p = tmp_path / "one_leaf.gff"
+    gf.gf_forest_save(G, p)
+    f = decode(p.read_bytes())
+    assert f["L"] == 0 and f["split_dim"].size == 0 and np.array_equal(f["X"], X)
+    H = gf.gf_forest_load(p)
+    _same_structure(gf, G, H)
+    ids, dists = gf.gf_query(H, torch.from_numpy(Q).cuda(), 5)
+    oi, od = oracle.bruteforce(X, Q, 5)
+    from parity import assert_topk_close
+    assert_topk_close(X, Q, ids.cpu().numpy(), dists.cpu().numpy(), oi, od)
