@@ -442,6 +442,8 @@ def ours(args):
         "clocks": best["clocks"],
         "fp32_plain": chosen["fp32"],
         "bf16_screen": chosen["bf16"],
+        "paths": {name: {key: chosen[name][key] for key in ("qps", "algo", "R", "achieved_gbs", "recall_at_1")}
+                  for name in ("fp32_stream", "bf16_stream", "fp32_leaf", "bf16_leaf") if name in chosen},
         "operating_points": {pid: {"bf16_qps": pt["bf16"]["qps"], "fp32_qps": pt["fp32"]["qps"],
                                    "recall_at_1": pt["bf16"]["recall_at_1"], "cand_per_query": pt["cand_per_query"]}
                              for pid, _, pt in points},
