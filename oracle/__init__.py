@@ -36,8 +36,9 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_LIB)
+        # GF_ORACLE_LIB: a prebuilt copy of the same source (e.g. a sanitizer build) to load instead
+        path = os.environ.get("GF_ORACLE_LIB") or build()
+        L = C.CDLL(path)
         i32, i64, u32, u64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
         P = C.c_void_p
         L.gfo_splitmix64_at.argtypes = [u64, u64]; L.gfo_splitmix64_at.restype = u64
@@ -171,6 +172,8 @@ def build_forest(X: np.ndarray, T: int, leaf_size: int, t: int = 5, shuffle: int
 def reflect(x: np.ndarray, u: np.ndarray) -> np.ndarray:
     """Px = x - 2 (u^T x) u (Sec. 2.2), with the rounding steps gfo_reflect fixes."""
     x, u = _f32(x), _f32(u)
+    if x.ndim != 1 or x.shape != u.shape:
+        raise ValueError("reflect takes one vector x and a vector u of the same length")
     out = np.empty_like(x)
     lib().gfo_reflect(_p(x), _p(u), x.shape[0], _p(out))
     return out
