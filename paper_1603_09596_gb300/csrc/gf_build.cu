@@ -23,6 +23,7 @@
 // deterministic); deeper levels use one CTA per node that keeps the node's keys in shared memory.
 #include "gf_internal.cuh"
 #include "gf_device.cuh"
+#include "gf_trace.cuh"
 
 #include <algorithm>
 #include <utility>
@@ -696,6 +697,7 @@ static int build_levels(gf_forest *F, const gf_rand_params &rp, uint64_t seed, c
 
     const int ndb = (F->d + DB - 1) / DB;
     for (int l = 0; l < L; ++l) {
+        GfRange level_range("gf_build: level");
         const long long cm = (n + (1ll << l) - 1) >> l;
         const long long nseg = (long long)T << l;
         if (cm <= SMALL) {
@@ -753,6 +755,7 @@ extern "C" int gf_build_reflected(const float *X, int64_t n, int32_t d, int32_t 
 
 static int build_any(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size, const gf_rand_params *rp_in,
                      uint64_t seed, const float *U_host, int32_t borrow_x, void *stream, gf_forest **out) {
+    GfRange range("gf_build");
     if (!out) return gf_fail(GF_EINVAL, "out is null");
     *out = nullptr;
     gf_rand_params rp;

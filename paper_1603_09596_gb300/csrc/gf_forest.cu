@@ -1,6 +1,7 @@
 // gf_forest.cu -- forest lifecycle (import, export, free), screening copies and the query entry
 // points of the C ABI.
 #include "gf_internal.cuh"
+#include "gf_trace.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -194,6 +195,7 @@ int gf_forest_fill_structure(gf_forest *F, const int32_t *split_dim_host, const 
 extern "C" int gf_forest_import(const float *X, int64_t n, int32_t d, int32_t T, int32_t leaf_size,
                                 const int32_t *split_dim_host, const float *split_val_host,
                                 const int32_t *perm_host, gf_forest **out) {
+    GfRange range("gf_forest_import");
     if (!out) return gf_fail(GF_EINVAL, "out is null");
     *out = nullptr;
     if (!split_dim_host || !split_val_host || !perm_host) return gf_fail(GF_EINVAL, "null host array");
@@ -321,6 +323,7 @@ __global__ void k_bf16_sqnorm(const __nv_bfloat16 *__restrict__ xb, long long n,
 }
 
 extern "C" int gf_forest_add_screen(gf_forest *F, int32_t precision, void *stream) {
+    GfRange range("gf_forest_add_screen");
     if (!F) return gf_fail(GF_EINVAL, "null forest");
     cudaStream_t st = (cudaStream_t)stream;
     int r;
@@ -349,6 +352,7 @@ extern "C" int gf_forest_add_screen(gf_forest *F, int32_t precision, void *strea
 
 extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_t k,
                            const gf_query_opts *o, int64_t *ids, float *dists) {
+    GfRange range("gf_query");
     if (!F) return gf_fail(GF_EINVAL, "null forest");
     if (m < 0) return gf_fail(GF_EINVAL, "m < 0");
     if (k < 1) return gf_fail(GF_EINVAL, "k=%d < 1", k);

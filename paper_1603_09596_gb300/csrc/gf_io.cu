@@ -25,6 +25,7 @@
 //     U      [T][d] f32   only with flag bit 0 (Sec. 2.2)
 //     X      [n][d] f32   the points
 #include "gf_internal.cuh"
+#include "gf_trace.cuh"
 
 #include <algorithm>
 #include <cerrno>
@@ -281,6 +282,7 @@ int load_impl(const std::string &path, gf_forest **out) {
 }  // namespace
 
 extern "C" int gf_forest_save(const gf_forest *F, const char *path) {
+    GfRange range("gf_forest_save");
     if (!F || !path || !*path) return gf_fail(GF_EINVAL, "null forest or empty path");
     if (!host_is_little_endian()) return gf_fail(GF_EUNSUPPORTED, "forest files need a little-endian host");
     try {
@@ -291,6 +293,7 @@ extern "C" int gf_forest_save(const gf_forest *F, const char *path) {
 }
 
 extern "C" int gf_forest_load(const char *path, gf_forest **out) {
+    GfRange range("gf_forest_load");
     if (!out) return gf_fail(GF_EINVAL, "out is null");
     *out = nullptr;
     if (!path || !*path) return gf_fail(GF_EINVAL, "empty path");

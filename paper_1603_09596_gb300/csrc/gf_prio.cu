@@ -17,6 +17,7 @@
 // never holds more than `budget` + 32 entries.  The output is the list of leaves in the order
 // checked, encoded (tree << L) | leaf.
 #include "gf_internal.cuh"
+#include "gf_trace.cuh"
 
 #include <algorithm>
 
@@ -223,6 +224,7 @@ int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int bud
 
 extern "C" int gf_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int32_t checks, double eps,
                               uint32_t *leaves, int32_t *nleaves, int32_t stride, void *stream) {
+    GfRange range("gf_prio_leaves");
     if (!F) return gf_fail(GF_EINVAL, "gf_prio_leaves: null forest");
     if (m < 0 || checks < 0 || !(eps >= 0.0)) return gf_fail(GF_EINVAL, "gf_prio_leaves: bad arguments");
     if (m == 0) return GF_OK;
