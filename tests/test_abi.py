@@ -55,3 +55,37 @@ def test_oracle_is_not_imported_by_the_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "gf_oracle" not in txt, f
+
+
+def test_every_entry_point_rejects_null_arguments_without_a_gpu(libpath):
+    """Argument checks come before any device work: a null forest, server or output is GF_EINVAL
+    (and freeing a null forest is a no-op), with no GPU in the process."""
+    import paper_1603_09596_gb300 as gf
+    L = gf.lib()
+    calls = {
+        "gf_query_ex": lambda: L.gf_query_ex(None, None, 1, 1, None, None, None),
+        "gf_query_workspace_size": lambda: L.gf_query_workspace_size(None, 1, None, None),
+        "gf_descend": lambda: L.gf_descend(None, None, 1, None, None),
+        "gf_candidates": lambda: L.gf_candidates(None, None, 1, None, None, None),
+        "gf_score_topk": lambda: L.gf_score_topk(None, None, 1, None, None, 1, 1, None, None, None),
+        "gf_score_screened": lambda: L.gf_score_screened(None, None, 1, None, None, 1, 1, None, None),
+        "gf_prio_leaves": lambda: L.gf_prio_leaves(None, None, 1, 1, 0.0, None, None, 1, None),
+        "gf_forest_import": lambda: L.gf_forest_import(None, 1, 1, 1, 1, None, None, None, None),
+        "gf_forest_export": lambda: L.gf_forest_export(None, None, None, None),
+        "gf_forest_get_info": lambda: L.gf_forest_get_info(None, None),
+        "gf_forest_add_screen": lambda: L.gf_forest_add_screen(None, 1, None),
+        "gf_forest_set_tuning": lambda: L.gf_forest_set_tuning(None, 0, 8, 0, 0, 0),
+        "gf_forest_set_reflections": lambda: L.gf_forest_set_reflections(None, None),
+        "gf_forest_save": lambda: L.gf_forest_save(None, b"f.gff"),
+        "gf_forest_load": lambda: L.gf_forest_load(None, None),
+        "gf_kernel_status": lambda: L.gf_kernel_status(None),
+        "gf_server_create": lambda: L.gf_server_create(None, 0, None, None),
+        "gf_server_submit": lambda: L.gf_server_submit(None, 0, None, 1, None),
+        "gf_server_poll": lambda: L.gf_server_poll(None, 0, None, None, 0),
+        "gf_server_get_stats": lambda: L.gf_server_get_stats(None, None),
+        "gf_build_ex": lambda: L.gf_build_ex(None, 10, 4, 2, 4, None, 0, 0, None, None),
+        "gf_build_reflected": lambda: L.gf_build_reflected(None, 10, 4, 2, 4, None, 0, None, 0, None, None),
+    }
+    bad = {name: code for name, code in ((n, f()) for n, f in calls.items()) if code != gf.GF_EINVAL}
+    assert not bad, bad
+    assert L.gf_forest_free(None) == gf.GF_OK
