@@ -445,3 +445,23 @@ def test_reflected_priority_search_matches_oracle(gf, name, c):
         assert np.array_equal(leaves[i, :onl[i]], oseq[i, :onl[i]])
     gi, gd = gf.gf_query(G, Qg, 10, checks=c)
     assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+
+
+@pytest.mark.parametrize("prec,algo", [("bf16", "stream"), ("bf16", "sort"), ("bf16", "leaf"),
+                                       ("fp8", "stream"), ("fp8", "sort")])
+def test_screen_reorders_the_hand_worked_pair_as_the_oracle(gf, prec, algo):
+    """The pair of test_screen_pins.SCREEN_FLIPS: a shortlist of one keeps the point the screen ranks
+    first (reported with its exact distance), a shortlist of two the exact nearest, on every path."""
+    from test_screen_pins import SCREEN_FLIPS
+    X, screen_first, exact_first = SCREEN_FLIPS[prec]
+    p = {"bf16": gf.GF_BF16_RERANK, "fp8": gf.GF_FP8_RERANK}[prec]
+    a = {"stream": gf.GF_ALGO_STREAM, "sort": gf.GF_ALGO_SORT, "leaf": gf.GF_ALGO_LEAF}[algo]
+    G = gf.gf_build(torch.from_numpy(X).cuda(), 1, 2, t=2, seed=0)
+    assert G.info.L == 0
+    gf.gf_forest_add_screen(G, p)
+    Q = torch.zeros((1, 2), dtype=torch.float32, device="cuda")
+    exact = (X.astype(np.float64) ** 2).sum(axis=1)
+    for R, want in ((1, screen_first), (2, exact_first)):
+        ids, d = gf.gf_query(G, Q, 1, precision=p, rerank_R=R, algo=a)
+        assert int(ids[0, 0]) == want, (R, ids)
+        assert abs(float(d[0, 0]) - exact[want]) <= RTOL * exact[want]

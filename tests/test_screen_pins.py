@@ -49,3 +49,34 @@ def test_screened_search_with_full_shortlist_is_exact_search():
         si, sd, _ = screen.screened_search(F, X, Q, 5, 10_000, prec)
         assert np.array_equal(si, ids)
         np.testing.assert_allclose(sd, d, rtol=1e-12)
+
+
+# Two points where the screen's rounding reverses the exact order (query at the origin), worked by
+# hand.  bf16 (8 significant bits): x1 = (1.0045, 0) rounds to (1.0078125, 0), screened 1.015686
+# against exact 1.009020; x2 = (1, 0.1) rounds to (1, 0.10009766), screened 1.010020 against exact
+# 1.01.  So the exact nearest is x1 but the screen ranks x2 first.  fp8 (row scale a / 448, codes
+# e4m3(x 448 / a)): x1 = (1, 0.06) has codes (448, 26) since 26.88 rounds to 26 (e4m3 steps of 2
+# in [16, 32)), dequantized (1, 0.0580357), screened 1.003368 against exact 1.0036; x2 =
+# (1.0017, 0) has codes (448, 0), screened and exact 1.003403.  So the exact nearest is x2 but the
+# screen ranks x1 first.  With a shortlist of one the screened search must return the point the
+# screen ranks first, reported with its exact distance; with a shortlist of two, the exact nearest.
+SCREEN_FLIPS = {
+    "bf16": (np.float32([[1.0045, 0.0], [1.0, 0.1]]), 1, 0),
+    "fp8": (np.float32([[1.0, 0.06], [1.0017, 0.0]]), 0, 1),
+}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_screen_rounding_reorders_a_hand_worked_pair(prec):
+    X, screen_first, exact_first = SCREEN_FLIPS[prec]
+    Q = np.zeros((1, 2), np.float32)
+    F = oracle.build_forest(X, 1, 2, t=2, seed=0)  # one leaf: both points are candidates
+    exact = (X.astype(np.float64) ** 2).sum(axis=1)
+    ids, d, shortlist = screen.screened_search(F, X, Q, 1, 1, prec)
+    assert ids[0, 0] == screen_first and d[0, 0] == exact[screen_first]
+    assert shortlist[0][0].tolist() == [screen_first]
+    ids2, d2, _ = screen.screened_search(F, X, Q, 1, 2, prec)
+    assert ids2[0, 0] == exact_first and d2[0, 0] == exact[exact_first]
+    screened = (screen.dequantized_rows(X, np.arange(2), prec) ** 2).sum(axis=1)
+    expect = {"bf16": [1.0156860351, 1.0100195408], "fp8": [1.0033682, 1.0034030]}[prec]
+    np.testing.assert_allclose(screened, expect, rtol=2e-7)
