@@ -210,6 +210,26 @@ def test_leaf_reflected_forest(gf):
     assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
 
 
+@pytest.mark.parametrize("c", [0, 24])
+def test_leaf_reflected_fp32_one_leaf_and_priority(gf, c):
+    # a reflected forest (Sec. 2.2) through the float32 leaf-major path: one leaf per tree (c = 0)
+    # and the priority search, against the oracle's reflected search
+    X, Q, F0 = case("tiny")
+    rng = np.random.default_rng(78)
+    U = rng.standard_normal((F0.T, F0.d))
+    U = (U / np.linalg.norm(U, axis=1, keepdims=True)).astype(np.float32)
+    F = oracle.build_forest(X, F0.T, F0.leaf_size, t=5, seed=9, U=U)
+    G = gpu_forest(gf, X, F)
+    gf.gf_forest_set_reflections(G, U)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, checks=c, algo=gf.GF_ALGO_LEAF)
+    if c:
+        oi, od, _, _ = oracle.search_priority(F, X, Q, 10, c)
+    else:
+        oi, od = oracle.search(F, X, Q, 10)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+    assert gf.gf_kernel_status() == 0
+
+
 @pytest.mark.parametrize("name", [c[0] for c in CASES])
 @pytest.mark.parametrize("k", [1, 10])
 def test_leaf_fp32_matches_oracle(gf, name, k):
