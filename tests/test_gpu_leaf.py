@@ -306,6 +306,31 @@ def test_leaf_priority_agrees_with_streaming(gf):
                       b[1].cpu().numpy().astype(np.float64))
 
 
+def test_leaf_at_its_limits(gf):
+    # the largest per-query key count the merge takes (T R = 256 x 32 = 8192 keys) and the largest
+    # bucket count the regrouping takes (T 2^L = 64 x 2^16 = 2^22 leaves), against the oracle
+    X, Q = synth.mixture(2000, 16, 300, "B", seed=5, qseed=6)
+    F = oracle.build_forest(X, 256, 16, t=5, seed=11)
+    assert F.T * 32 == 8192
+    G = gpu_forest(gf, X, F)
+    Qg = torch.from_numpy(Q).cuda()
+    gi, gd = gf.gf_query(G, Qg, 32, algo=gf.GF_ALGO_LEAF)
+    oi, od = oracle.search(F, X, Q, 32)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+    gi, gd = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF)
+    oi, od, cands = oracle_screen(F, X, Q, 10, 32)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+
+    X, Q = synth.mixture(65_536, 8, 2000, "A", seed=7, qseed=8)
+    F = oracle.build_forest(X, 64, 1, t=5, seed=13)
+    assert F.L == 16 and F.T << F.L == 1 << 22
+    G = gpu_forest(gf, X, F)
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 5, algo=gf.GF_ALGO_LEAF)
+    oi, od = oracle.search(F, X, Q, 5)
+    assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
+    assert gf.gf_kernel_status() == 0
+
+
 def test_leaf_rejects_what_it_does_not_run(gf):
     X, Q, F = case("tiny")
     G = gpu_forest(gf, X, F)
