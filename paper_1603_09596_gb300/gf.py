@@ -263,6 +263,7 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
              rows_in_flight: int = 0, order: int = GF_ORDER_AUTO, checks: int = 0, eps: float = 0.0,
              out: tuple[torch.Tensor, torch.Tensor] | None = None):
     """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k])."""
+    qp = _dptr(Q, torch.float32, "Q")
     m = Q.shape[0]
     if out is None:
         ids = torch.empty((m, k), dtype=torch.int64, device=Q.device)
@@ -271,7 +272,7 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
         ids, dists = out
     o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
               rows_in_flight, order, checks, eps)
-    _check(lib().gf_query_ex(F.handle, _dptr(Q, torch.float32, "Q"), m, k, C.byref(o),
+    _check(lib().gf_query_ex(F.handle, qp, m, k, C.byref(o),
                              _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists")))
     return ids, dists
 

@@ -89,3 +89,18 @@ def test_every_entry_point_rejects_null_arguments_without_a_gpu(libpath):
     bad = {name: code for name, code in ((n, f()) for n, f in calls.items()) if code != gf.GF_EINVAL}
     assert not bad, bad
     assert L.gf_forest_free(None) == gf.GF_OK
+
+
+def test_binding_rejects_host_tensors_without_a_gpu(libpath):
+    """The binding passes device pointers only: a host tensor is refused before any CUDA call."""
+    import torch
+    import paper_1603_09596_gb300 as gf
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        gf.gf_build(torch.zeros(10, 4), 2, 4)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        gf.gf_query(gf.Forest(None), torch.zeros(2, 4), 1)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        gf.gf_forest_import(torch.zeros(10, 4), 2, 4, [[0]], [[0.0]], [[0]])
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_forest_load(os.path.join(ROOT, "no_such_dir", "f.gff"))
+    assert e.value.code == gf.GF_EIO
