@@ -88,7 +88,11 @@ int gf_forest_alloc(gf_forest **out, const float *X, int64_t n, int32_t d, int32
     gf_forest *F = new gf_forest();
     F->n = n; F->d = d; F->T = T; F->leaf_size = leaf_size;
     F->L = depth_of(n, leaf_size);
-    if (F->L > 30) { delete F; return gf_fail(GF_EINVAL, "tree depth %d too large", F->L); }
+    if (F->L > 30) {
+        const int32_t L = F->L;
+        delete F;
+        return gf_fail(GF_EINVAL, "tree depth %d too large", L);
+    }
     F->max_leaf = (int32_t)((n + ((int64_t)1 << F->L) - 1) >> F->L);
     const int64_t cap = (int64_t)T * F->max_leaf;
     if (cap > (1 << 24)) { delete F; return gf_fail(GF_EINVAL, "T * leaf size = %lld too large", (long long)cap); }

@@ -104,3 +104,15 @@ def test_binding_rejects_host_tensors_without_a_gpu(libpath):
     with pytest.raises(gf.GFError) as e:
         gf.gf_forest_load(os.path.join(ROOT, "no_such_dir", "f.gff"))
     assert e.value.code == gf.GF_EIO
+
+
+def test_too_deep_forest_is_rejected_before_any_device_work(libpath):
+    # n > 2^30 points in leaves of one point would need depth 31: refused from the shape alone
+    import numpy as np
+    import paper_1603_09596_gb300 as gf
+    L = gf.lib()
+    one = np.zeros(1, np.int32)
+    code = L.gf_forest_import(16, (1 << 30) + 1, 1, 1, 1, one.ctypes.data, one.ctypes.data, one.ctypes.data,
+                              ctypes.byref(ctypes.c_void_p()))
+    assert code == gf.GF_EINVAL
+    assert b"tree depth 31 too large" in L.gf_last_error()
