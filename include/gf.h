@@ -191,8 +191,8 @@ int gf_forest_get_info(const gf_forest *F, gf_forest_info *info);
  * i32 d, T, leaf_size, L, u32 flags (1 reflections, 2 bf16 screen, 4 fp8 screen), i32 tuning
  * warps[3] ctas[3] rerank_R[3] rows_in_flight[3], u32 0, u64 payload bytes, u64 s1, u64 s2,
  * u64 0 -- then nodes [T][2^L - 1] x (i32 dim, f32 value), perm [T][n] i32, U [T][d] f32 (flag 1
- * only), X [n][d] f32.  s1 = sum w_i and s2 = sum (i + 1) w_i (mod 2^64) over the payload's u32
- * words w_0, w_1, ...
+ * only), X [n][d] f32.  s1 = sum w_i and s2 = sum (i + 1) w_i (mod 2^64), the w_i the u32 words of
+ * header bytes 0..95 followed by those of the payload.
  * Errors: GF_EINVAL (null forest or empty path), GF_EIO (the file cannot be created or written;
  * no partial file is left), GF_ENOMEM, GF_ECUDA.  Synchronous.
  */

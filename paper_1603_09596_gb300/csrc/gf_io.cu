@@ -16,8 +16,8 @@
 //    44  i32 x 12  tuning per precision: warps[3], ctas[3], rerank_R[3], rows_in_flight[3]
 //    92  u32       0
 //    96  u64       payload bytes
-//   104  u64 x 2   checksum s1 = sum w_i, s2 = sum (i + 1) w_i (mod 2^64) over the payload read as
-//                  u32 words w_0, w_1, ...
+//   104  u64 x 2   checksum s1 = sum w_i, s2 = sum (i + 1) w_i (mod 2^64), the w_i the u32 words of
+//                  header bytes 0..95 followed by those of the payload
 //   120  u64       0
 //   payload
 //     nodes  [T][2^L - 1] x (i32 split dimension, f32 split value)   (Alg. 1: one split per node)
@@ -42,6 +42,7 @@ constexpr char MAGIC[8] = {'G', 'F', 'F', 'O', 'R', 'E', 'S', 'T'};
 constexpr uint32_t VERSION = 1;
 constexpr uint32_t BOM = 0x01020304u;
 constexpr size_t HEADER_BYTES = 128;
+constexpr size_t HEADER_SUMMED = 96;  // header bytes covered by the checksum (all but its own fields)
 constexpr uint32_t FLAG_U = 1u, FLAG_BF16 = 2u, FLAG_FP8 = 4u;
 
 void put32(unsigned char *b, size_t off, uint32_t v) {
@@ -68,8 +69,8 @@ bool host_is_little_endian() {
     return c == 1;
 }
 
-// Position-weighted sums of the payload's u32 words (a Fletcher-style check: catches changed,
-// dropped and swapped words).
+// Position-weighted sums of u32 words (a Fletcher-style check: catches changed, dropped and
+// swapped words).
 struct Checksum {
     uint64_t s1 = 0, s2 = 0, words = 0;
     void add(const void *p, size_t bytes) {
@@ -134,8 +135,24 @@ int save_impl(const gf_forest *F, const std::string &path) {
     w.f = std::fopen(tmp.c_str(), "wb");
     if (!w.f) return io_fail("cannot create", tmp);
     unsigned char hdr[HEADER_BYTES] = {};
+    std::memcpy(hdr, MAGIC, 8);
+    put32(hdr, 8, VERSION);
+    put32(hdr, 12, BOM);
+    put64(hdr, 16, (uint64_t)F->n);
+    put32(hdr, 24, (uint32_t)F->d);
+    put32(hdr, 28, (uint32_t)F->T);
+    put32(hdr, 32, (uint32_t)F->leaf_size);
+    put32(hdr, 36, (uint32_t)F->L);
+    put32(hdr, 40, (F->U ? FLAG_U : 0) | (F->xb ? FLAG_BF16 : 0) | (F->x8 ? FLAG_FP8 : 0));
+    for (int p = 0; p < 3; ++p) {
+        put32(hdr, 44 + 4 * p, (uint32_t)F->tune_warps[p]);
+        put32(hdr, 56 + 4 * p, (uint32_t)F->tune_ctas[p]);
+        put32(hdr, 68 + 4 * p, (uint32_t)F->tune_R[p]);
+        put32(hdr, 80 + 4 * p, (uint32_t)F->tune_G[p]);
+    }
     bool ok = std::fwrite(hdr, 1, HEADER_BYTES, w.f) == HEADER_BYTES;
     w.ck = Checksum();
+    w.ck.add(hdr, HEADER_SUMMED);  // the header's fields, then the payload
     ok = ok && w.write(nodes.data(), nodes.size() * sizeof(int2));
     ok = ok && w.write(perm.data(), perm.size() * 4);
     ok = ok && w.write(U.data(), U.size() * 4);
@@ -151,22 +168,7 @@ int save_impl(const gf_forest *F, const std::string &path) {
         ok = w.write(slab.data(), rows * d * 4);
     }
     if (ok) {
-        std::memcpy(hdr, MAGIC, 8);
-        put32(hdr, 8, VERSION);
-        put32(hdr, 12, BOM);
-        put64(hdr, 16, (uint64_t)F->n);
-        put32(hdr, 24, (uint32_t)F->d);
-        put32(hdr, 28, (uint32_t)F->T);
-        put32(hdr, 32, (uint32_t)F->leaf_size);
-        put32(hdr, 36, (uint32_t)F->L);
-        put32(hdr, 40, (F->U ? FLAG_U : 0) | (F->xb ? FLAG_BF16 : 0) | (F->x8 ? FLAG_FP8 : 0));
-        for (int p = 0; p < 3; ++p) {
-            put32(hdr, 44 + 4 * p, (uint32_t)F->tune_warps[p]);
-            put32(hdr, 56 + 4 * p, (uint32_t)F->tune_ctas[p]);
-            put32(hdr, 68 + 4 * p, (uint32_t)F->tune_R[p]);
-            put32(hdr, 80 + 4 * p, (uint32_t)F->tune_G[p]);
-        }
-        put64(hdr, 96, w.ck.words * 4);
+        put64(hdr, 96, w.ck.words * 4 - HEADER_SUMMED);
         put64(hdr, 104, w.ck.s1);
         put64(hdr, 112, w.ck.s2);
         ok = std::fseek(w.f, 0, SEEK_SET) == 0 && std::fwrite(hdr, 1, HEADER_BYTES, w.f) == HEADER_BYTES &&
@@ -233,6 +235,7 @@ int load_impl(const std::string &path, gf_forest **out) {
         return gf_fail(GF_EIO, "'%s': %lld bytes, expected %llu (truncated or trailing data)", path.c_str(), size,
                        (unsigned long long)(HEADER_BYTES + expect));
     if (std::fseek(rd.f, (long)HEADER_BYTES, SEEK_SET) != 0) return io_fail("cannot seek in", path);
+    rd.ck.add(hdr, HEADER_SUMMED);
 
     std::vector<int2> nodes((size_t)T * nn);
     std::vector<int32_t> perm((size_t)T * n);

@@ -38,13 +38,13 @@ def encode(n, d, T, leaf_size, L, split_dim, split_val, perm, X, U=None, flags=0
         parts.append(np.ascontiguousarray(U, dtype="<f4").tobytes())
     parts.append(np.ascontiguousarray(X, dtype="<f4").tobytes())
     payload = b"".join(parts)
-    s1, s2 = checksum(payload) if checks is None else checks
     h = bytearray(HEADER)
     h[0:8] = MAGIC
     h[8:16] = np.array([version, 0x01020304], dtype="<u4").tobytes()
     h[16:24] = np.array([n], dtype="<i8").tobytes()
     h[24:44] = np.array([d, T, leaf_size, L, flags], dtype="<u4").tobytes()
     h[44:92] = np.array(tuning, dtype="<i4").reshape(-1).tobytes()
+    s1, s2 = checksum(bytes(h[:96]) + payload) if checks is None else checks
     h[96:120] = np.array([len(payload) if payload_bytes is None else payload_bytes, s1, s2],
                          dtype="<u8").tobytes()
     return bytes(h) + payload
@@ -60,7 +60,7 @@ def decode(blob: bytes):
     payload_bytes, s1, s2 = (int(v) for v in np.frombuffer(blob, "<u8", 3, 96))
     payload = blob[HEADER:]
     assert len(payload) == payload_bytes
-    assert checksum(payload) == (s1, s2)
+    assert checksum(blob[:96] + payload) == (s1, s2)
     nn = (1 << L) - 1
     off = 0
 
@@ -149,6 +149,8 @@ def _mutations(small):
     w = np.frombuffer(good[HEADER:], "<u4").copy()
     w[[0, 1]] = w[[1, 0]]
     swapped = good[:HEADER] + w.tobytes()
+    retuned = bytearray(good)
+    retuned[44:48] = np.array([4], "<i4").tobytes()  # a valid tuning value, but not the one summed
     return {
         "empty": b"",
         "short_header": good[:100],
@@ -164,6 +166,7 @@ def _mutations(small):
         "bit_flip": bytes(flip),
         "swapped_words": swapped,
         "checksum": forest_blob(small, checks=(1, 2)),
+        "header_field": bytes(retuned),
         "zero_trees": encode(F.n, F.d, 0, F.leaf_size, F.L, np.zeros((0, nn)), np.zeros((0, nn)),
                              np.zeros((0, F.n)), X),
     }
@@ -171,7 +174,7 @@ def _mutations(small):
 
 @pytest.mark.parametrize("kind", ["empty", "short_header", "magic", "version", "byte_order", "depth", "flags",
                                   "tuning", "payload_size", "truncated", "trailing", "bit_flip",
-                                  "swapped_words", "checksum", "zero_trees"])
+                                  "swapped_words", "checksum", "header_field", "zero_trees"])
 def test_malformed_file_is_eio(gf, small, tmp_path, kind):
     p = tmp_path / f"{kind}.gff"
     p.write_bytes(_mutations(small)[kind])
