@@ -103,6 +103,11 @@ typedef struct gf_query_opts {
     int32_t checks;          /* the paper's c, max. leaf checks (Alg. 2, Sec. 3 "Parameters");
                                 <= T: one leaf per tree (the default search) */
     double eps;              /* the paper's epsilon >= 0: c / (1 + eps) leaves are checked */
+    void *events;            /* optional, for timing: two cudaEvent_t (created by the caller); the
+                                query records events[0] on `stream` just before the first launch of
+                                its scoring kernel (k_leaf_score / k_leaf_f32 on the leaf-major path,
+                                else the streaming or sort query kernel) and events[1] just after the
+                                last, so that kernel can be timed alone; NULL: no events */
 } gf_query_opts;
 
 typedef struct gf_forest gf_forest; /* opaque; owned by the library */
@@ -220,7 +225,8 @@ int gf_forest_add_screen(gf_forest *F, int32_t precision, void *stream);
 
 /* Set the forest's default kernel shape and shortlist for one precision (what the autotuner
  * writes); gf_query_ex uses them where its options hold 0.  rerank_R / rows_in_flight 0 keep the
- * current value. */
+ * current value.  Limits: 1 <= warps_per_cta <= 32, 0 <= ctas_per_sm <= 32, 0 <= rerank_R <= 2048,
+ * rows_in_flight 0, 2 or 4 (else GF_EINVAL); forest files are held to the same limits. */
 int gf_forest_set_tuning(gf_forest *F, int32_t precision, int32_t warps_per_cta,
                          int32_t ctas_per_sm, int32_t rerank_R, int32_t rows_in_flight);
 
@@ -272,12 +278,16 @@ int gf_kernel_status(int32_t *status);
  *
  * The kernel's scratch (one seen-bitmap of ceil(n / 32) 32-bit words per CTA) comes from a static
  * device array of GF_NOALLOC_SCRATCH_BYTES that is part of the library image: every GPU that loads
- * the library holds it until the process exits.  The queries run in consecutive launches of at
- * most GF_NOALLOC_SCRATCH_BYTES / (4 * ceil(n / 32)) rows each, so a forest of more than
+ * the library holds it until the process exits.  The queries run in consecutive launches, each of
+ * as many rows as its whole scratch layout fits in the array (the bitmaps of its CTAs, plus 12 bytes
+ * a query when the launch reorders its queries for locality), so a forest of more than
  * 8 * GF_NOALLOC_SCRATCH_BYTES points (536,870,912) is rejected with GF_EINVAL.  Arguments,
  * outputs and errors are those of gf_query_ex; precision and rerank_R as in gf_query_opts.
  *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress) with
- *    that device current; make that first call before any stream capture on the device.
+ *    that device current; make that first call before any stream capture on the device.  Under
+ *    CUDA's lazy module loading that lookup is also when the driver loads the library's module on
+ *    the device and sets the array aside: device free memory drops by GF_NOALLOC_SCRATCH_BYTES at
+ *    the first call, and never during later calls.
  *  - The array is shared by every call in the process and keeps what the last call left in it;
  *    each call clears the part it uses before its kernels run.  Calls whose work overlaps on the GPU
  *    (on different streams, or from several threads) race on the array and give wrong answers:
@@ -399,6 +409,28 @@ int gf_server_destroy(gf_server *S);
  * Errors: GF_EINVAL, GF_EUNSUPPORTED (T * 2^L > 2^32, budget above 4096). */
 int gf_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int32_t checks, double eps,
                    uint32_t *leaves, int32_t *nleaves, int32_t stride, void *stream);
+
+/* ---------------------------------------------------------------- failure injection (tests)
+ * Hooks that make the library's failure paths run on purpose, for tests of its error handling
+ * without a device fault.  The paper has no counterpart.  Both settings are process-wide and apply
+ * to calls made after them.
+ */
+
+/* The (after + 1)-th device allocation the library makes from now on fails as if the device had no
+ * memory left: the call that made it returns GF_ENOMEM after releasing what it had allocated (a
+ * failed build leaves no forest, *out stays NULL).  One failure, then the hook disarms itself;
+ * after < 0 disarms it at once.  Counts the allocations of forest storage and build scratch
+ * (gf_build*, gf_forest_import, gf_forest_load, gf_forest_add_screen, gf_forest_set_reflections).
+ * Errors: none (GF_OK). */
+int gf_debug_fail_alloc(int32_t after);
+
+/* Time limit, in nanoseconds, of the waits of the leaf-major tensor-core scoring kernel's pipeline
+ * (0: the default, about two seconds).  A wait that runs out records GF_ETIMEOUT for
+ * gf_kernel_status; every role of the kernel then leaves its loop, its copies and tensor-core
+ * operations are drained (under the default limit, whatever this one) and its tensor memory freed.
+ * The results of a query whose kernel gave up are unspecified, but its reads and writes stay in
+ * bounds.  A limit of a few hundred nanoseconds makes the waits run out.  Errors: none (GF_OK). */
+int gf_debug_set_wait_limit(uint64_t ns);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -1,6 +1,8 @@
 // gf_forest.cu -- forest lifecycle (import, export, free), screening copies and the query entry
 // points of the C ABI.
 #include "gf_internal.cuh"
+
+#include <atomic>
 #include "gf_trace.cuh"
 
 #include <algorithm>
@@ -30,9 +32,24 @@ int gf_cuda_fail(cudaError_t e, const char *what) {
     return gf_fail(code, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// gf_debug_fail_alloc: the number of library allocations that still succeed before one fails
+// (-1: none fails)
+static std::atomic<int> g_alloc_countdown{-1};
+
+extern "C" int gf_debug_fail_alloc(int32_t after) {
+    g_alloc_countdown.store(after < 0 ? -1 : after);
+    return GF_OK;
+}
+
 int gf_dmalloc(void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return GF_OK;
+    for (int c = g_alloc_countdown.load(); c >= 0;) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+            if (c == 0) return gf_fail(GF_ENOMEM, "cudaMalloc(%zu bytes): refused (gf_debug_fail_alloc)", bytes);
+            break;
+        }
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -71,6 +88,7 @@ static void forest_release(gf_forest *F) {
     cudaFree(F->xbn);
     cudaFree(F->x8);
     cudaFree(F->scale8);
+    cudaFree(F->x8n);
     cudaFree(F->U);
     delete F;
 }
@@ -266,7 +284,8 @@ extern "C" int gf_forest_free(gf_forest *F) {
 extern "C" int gf_forest_set_tuning(gf_forest *F, int32_t precision, int32_t warps_per_cta,
                                     int32_t ctas_per_sm, int32_t rerank_R, int32_t rows_in_flight) {
     if (!F || precision < 0 || precision > 2) return gf_fail(GF_EINVAL, "bad forest or precision");
-    if (warps_per_cta < 1 || warps_per_cta > 32 || ctas_per_sm < 0 || rerank_R < 0 ||
+    if (warps_per_cta < 1 || warps_per_cta > 32 || ctas_per_sm < 0 || ctas_per_sm > GF_MAX_CTAS_PER_SM ||
+        rerank_R < 0 || rerank_R > GF_MAX_SHORTLIST ||
         (rows_in_flight != 0 && rows_in_flight != 2 && rows_in_flight != 4))
         return gf_fail(GF_EINVAL, "bad tuning values");
     F->tune_warps[precision] = warps_per_cta;
@@ -326,6 +345,24 @@ __global__ void k_bf16_sqnorm(const __nv_bfloat16 *__restrict__ xb, long long n,
     }
 }
 
+// x8n[i] = sum_j (scale_i x8[i][j])^2, accumulated in float64 and rounded once: a warp per row.
+__global__ void k_fp8_sqnorm(const uint8_t *__restrict__ x8, const float *__restrict__ scale, long long n, int ld8,
+                             float *x8n) {
+    const int lane = threadIdx.x & 31;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += ((long long)gridDim.x * blockDim.x) >> 5) {
+        double acc = 0.0;
+        for (int j = lane; j < ld8; j += 32) {
+            const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)x8[i * ld8 + j], __NV_E4M3);
+            const double v = (double)__half2float(*reinterpret_cast<const __half *>(&h));
+            acc += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double sc = (double)scale[i];
+        if (lane == 0) x8n[i] = (float)(acc * sc * sc);
+    }
+}
+
 extern "C" int gf_forest_add_screen(gf_forest *F, int32_t precision, void *stream) {
     GfRange range("gf_forest_add_screen");
     if (!F) return gf_fail(GF_EINVAL, "null forest");
@@ -342,8 +379,16 @@ extern "C" int gf_forest_add_screen(gf_forest *F, int32_t precision, void *strea
         if (F->x8) return GF_OK;
         if ((r = gf_dmalloc((void **)&F->x8, (size_t)F->n * F->ld8))) return r;
         if ((r = gf_dmalloc((void **)&F->scale8, (size_t)F->n * 4))) { cudaFree(F->x8); F->x8 = nullptr; return r; }
+        if ((r = gf_dmalloc((void **)&F->x8n, (size_t)F->n * 4))) {
+            cudaFree(F->x8);
+            cudaFree(F->scale8);
+            F->x8 = nullptr;
+            F->scale8 = nullptr;
+            return r;
+        }
         k_to_fp8<<<F->num_sms * 8, 256, 0, st>>>(F->x, F->ldx, F->n, F->d, F->ld8, F->x8, F->scale8);
-        F->device_bytes += (int64_t)F->n * F->ld8 + F->n * 4;
+        k_fp8_sqnorm<<<F->num_sms * 8, 256, 0, st>>>(F->x8, F->scale8, F->n, F->ld8, F->x8n);
+        F->device_bytes += (int64_t)F->n * F->ld8 + F->n * 8;
     } else {
         return gf_fail(GF_EINVAL, "precision %d has no screening copy", precision);
     }
@@ -385,6 +430,7 @@ extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_
     x.order = o->order;
     if (o->checks < 0 || !(o->eps >= 0.0)) return gf_fail(GF_EINVAL, "checks < 0 or eps < 0");
     x.leaf_budget = leaf_budget_of(F, o->checks, o->eps);
+    x.events = (cudaEvent_t *)o->events;
     if (x.leaf_budget > 0) {
         if (((unsigned long long)F->T << F->L) > 0xffffffffull)
             return gf_fail(GF_EUNSUPPORTED, "priority search needs T * 2^L <= 2^32");
@@ -392,9 +438,6 @@ extern "C" int gf_query_ex(const gf_forest *F, const float *Q, int64_t m, int32_
     }
     return gf_launch_query(F, Q, m, k, p, R, warps, cps, (cudaStream_t)o->stream, ids, dists, x);
 }
-
-int gf_stream_grid(const gf_forest *F, int64_t m, int warps, int ctas_per_sm, int precision, int k, int R,
-                   long long *grid);
 
 extern "C" int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_query_opts *o, int64_t *bytes) {
     if (!F || !bytes) return gf_fail(GF_EINVAL, "null argument");
@@ -411,7 +454,9 @@ extern "C" int gf_query_workspace_size(const gf_forest *F, int64_t m, const gf_q
     long long grid = 0;
     int r = gf_stream_grid(F, m, warps, cps, p, 1, R, &grid);
     if (r) return r;
-    const bool ordered = o->order == GF_ORDER_LOCALITY || (o->order == GF_ORDER_AUTO && m > grid);
+    // A launch's own grid can be below this one (a larger k or R lowers the occupancy), and AUTO
+    // reorders every batch longer than the launch's grid: count the order arrays for any m > 1.
+    const bool ordered = o->order == GF_ORDER_LOCALITY || (o->order == GF_ORDER_AUTO && m > 1);
     if ((r = gf_stream_workspace_bytes(F, m, grid, ordered, leaf_budget_of(F, o->checks, o->eps), bytes))) return r;
     if (o->algo == GF_ALGO_LEAF || o->algo == GF_ALGO_AUTO) {
         // the leaf-major path's scratch; AUTO gets the larger of the two

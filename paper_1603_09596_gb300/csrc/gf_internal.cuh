@@ -20,6 +20,7 @@
 //   xbn     float [n]             |xb_i|^2 (float64 sum rounded once), with xb
 //   x8      e4m3  [n][ld8]        optional screening copy, ld8 = round_up(d, 16)
 //   scale8  float [n]             per-row scale of x8
+//   x8n     float [n]             |scale8_i x8_i|^2 (float64 sum rounded once), with x8
 struct gf_forest {
     int64_t n = 0;
     int32_t d = 0, T = 0, leaf_size = 0, L = 0;
@@ -33,6 +34,7 @@ struct gf_forest {
     float *xbn = nullptr;
     uint8_t *x8 = nullptr;
     float *scale8 = nullptr;
+    float *x8n = nullptr;
     float *U = nullptr;  // [T][d] Householder vectors (Sec. 2.2), or null: trees on X itself
     int device = 0;
     int num_sms = 0;
@@ -44,6 +46,11 @@ struct gf_forest {
     int64_t device_bytes = 0;
 };
 
+// Limits of the tuning values (gf_forest_set_tuning, forest files): an SM runs at most 32 CTAs,
+// and the streaming kernel keeps at most 2048 keys (k or R) per query.
+constexpr int32_t GF_MAX_CTAS_PER_SM = 32;
+constexpr int32_t GF_MAX_SHORTLIST = 2048;
+
 // Read-only view handed to kernels by value.
 struct ForestView {
     const float *x;
@@ -51,6 +58,7 @@ struct ForestView {
     const float *xbn;
     const uint8_t *x8;
     const float *scale8;
+    const float *x8n;
     const float *U;  // [T][d] or null
     const int2 *nodes;
     const int32_t *perm;
@@ -60,7 +68,7 @@ struct ForestView {
 
 inline ForestView view_of(const gf_forest *F) {
     ForestView v;
-    v.x = F->x; v.xb = F->xb; v.xbn = F->xbn; v.x8 = F->x8; v.scale8 = F->scale8; v.U = F->U;
+    v.x = F->x; v.xb = F->xb; v.xbn = F->xbn; v.x8 = F->x8; v.scale8 = F->scale8; v.x8n = F->x8n; v.U = F->U;
     v.nodes = F->nodes; v.perm = F->perm;
     v.n = F->n; v.d = F->d; v.ldx = F->ldx; v.ldb = F->ldb; v.ld8 = F->ld8;
     v.T = F->T; v.L = F->L; v.nnodes = (1 << F->L) - 1;
@@ -132,13 +140,22 @@ struct QueryExtra {
     int32_t rows_in_flight = 0;
     int32_t order = GF_ORDER_AUTO;
     int32_t leaf_budget = 0;  // leaves per query for the priority search (0: one per tree)
+    cudaEvent_t *events = nullptr;  // recorded around the scoring kernel's launches (timing)
 };
+
+// Record events[i] on st when the caller asked for timing events.
+inline cudaError_t gf_record(const QueryExtra &x, int i, cudaStream_t st) {
+    return x.events ? cudaEventRecord(x.events[i], st) : cudaSuccess;
+}
 
 int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int budget, unsigned *leaves,
                           int *nleaves, cudaStream_t st);
 size_t gf_prio_smem_bytes(int budget, int T);
 int gf_stream_workspace_bytes(const gf_forest *F, int64_t m, long long grid, bool ordered, int leaf_budget,
                               int64_t *bytes);
+// CTAs of a streaming launch of m queries with this shape (warps, ctas_per_sm 0 = occupancy limit)
+int gf_stream_grid(const gf_forest *F, int64_t m, int warps, int ctas_per_sm, int precision, int k, int R,
+                   long long *grid);
 
 // Leaves the priority search checks per query: max(T, ceil(checks / (1 + eps))), 0 when that is T.
 inline int32_t leaf_budget_of(const gf_forest *F, int32_t checks, double eps) {
@@ -153,7 +170,7 @@ inline int32_t leaf_budget_of(const gf_forest *F, int32_t checks, double eps) {
 // leaf_budget > 0: the priority search's leaves (QueryExtra::leaf_budget), else one leaf per tree.
 int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision, int32_t R,
                    int32_t order, int32_t leaf_budget, cudaStream_t st, int64_t *ids, float *dists,
-                   void *workspace, int64_t workspace_bytes);
+                   void *workspace, int64_t workspace_bytes, cudaEvent_t *events = nullptr);
 int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order,
                                 int32_t leaf_budget);
 // Whether GF_ALGO_AUTO takes the leaf-major path for this batch.

@@ -110,7 +110,9 @@ struct Reader {
 
 bool tuning_ok(const int32_t w[3], const int32_t c[3], const int32_t r[3], const int32_t g[3]) {
     for (int p = 0; p < 3; ++p)
-        if (w[p] < 1 || w[p] > 32 || c[p] < 0 || r[p] < 0 || (g[p] != 0 && g[p] != 2 && g[p] != 4)) return false;
+        if (w[p] < 1 || w[p] > 32 || c[p] < 0 || c[p] > GF_MAX_CTAS_PER_SM || r[p] < 0 || r[p] > GF_MAX_SHORTLIST ||
+            (g[p] != 0 && g[p] != 2 && g[p] != 4))
+            return false;
     return true;
 }
 

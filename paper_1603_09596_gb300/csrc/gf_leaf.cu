@@ -45,39 +45,59 @@
 #include "gf_score.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 
 __device__ int g_kernel_status = 0;  // first error a kernel of the library recorded
 
+// gf_debug_set_wait_limit: the scoring kernel's wait limit in nanoseconds (0: WAIT_NS)
+static std::atomic<unsigned long long> g_wait_limit_ns{0};
+
 namespace {
 
-constexpr int NQ = 16;           // queries per chunk (the MMA's N is 2 NQ: parts hi and lo)
+constexpr int NQ = 16;           // queries per chunk (the MMA's N is QP NQ: the queries' parts)
 constexpr int BM = 128;          // leaf rows per tile: the MMA's M, one tensor-memory lane each
-constexpr int BK = 64;           // bf16 values per sub-tile: one 128-byte swizzled row
-constexpr int SUB = 3;           // sub-tiles per pipeline stage: one wait and one release per SUB k-steps
-constexpr int STAGES = 3;        // shared-memory pipeline depth
-constexpr int PROD_WARPS = 9;    // producer warps; each loads whole sub-tiles, one at a time
 constexpr int R_MAX = 32;        // longest shortlist per (query, tree): one key per lane
-constexpr int A_BYTES = BM * 128;
-constexpr int B_BYTES = NQ * 128;
-constexpr int SUBTILE_BYTES = A_BYTES + 2 * B_BYTES;  // leaf rows, then one B tile of MMA_N rows: hi, lo
-constexpr int STAGE_BYTES = SUB * SUBTILE_BYTES;
-constexpr int MMA_N = 2 * NQ;                       // the query parts hi and lo side by side
-constexpr int TMEM_COLS = 2 * MMA_N;                // two accumulators of MMA_N float32 columns
-constexpr int EPI_THREADS = 128;                        // warps 0-3: tensor-memory lane quadrants 0-3
-constexpr int MMA_WARP = 4 + PROD_WARPS;                  // warps 4 .. 3 + PROD_WARPS load
-constexpr int THREADS = (MMA_WARP + 1) * 32;
-constexpr int MAX_KEYS = 8192;                      // T * R limit of the merge
-static_assert(SUBTILE_BYTES % 1024 == 0, "sub-tiles must keep the 1024-byte swizzle alignment");
-static_assert(PROD_WARPS <= STAGES * SUB, "every producer warp needs a sub-tile of its own");
+constexpr int EPI_THREADS = 128; // warps 0-3: tensor-memory lane quadrants 0-3
+constexpr int MAX_KEYS = 8192;   // T * R limit of the merge
 
-// shared-memory plan of k_leaf_score (offsets from a 1024-aligned base)
-constexpr int SM_STAGES = 0;
-constexpr int SM_WL = SM_STAGES + STAGES * STAGE_BYTES;  // the epilogue warps' lists [4][NQ][32]
-constexpr int SM_BAR = SM_WL + 4 * NQ * 32 * 8;           // full[STAGES] empty[STAGES] dfull[2] dempty[2] fin
-constexpr int SM_MISC = SM_BAR + (2 * STAGES + 5) * 8;  // tensor-memory base, abort flag
-constexpr int SM_TOTAL = SM_MISC + 16;
-constexpr int SMEM_BYTES = SM_TOTAL + 1024;  // slack for aligning the base
+// Screen formats of the tensor-core scoring kernel.
+//   bf16: the points' bf16 copy against the query's parts hi = bf16(q), lo = bf16(q - hi)
+//         (kind::f16, K = 16 per MMA);
+//   fp8:  the points' E4M3 codes (row scale s_x) against three E4M3 parts of the query with
+//         scales c, c/16, c/256 (c a power of two, q ~ c (p0 + p1/16 + p2/256)): kind::f8f6f4,
+//         K = 32 per MMA, so a row tile takes half the instructions and half the bytes.
+constexpr int LF_BF16 = 0, LF_FP8 = 1;
+
+template <int FMT>
+struct LeafCfg {
+    static constexpr int QP = FMT == LF_FP8 ? 3 : 2;       // query parts
+    static constexpr int ESZ = FMT == LF_FP8 ? 1 : 2;      // bytes per value
+    static constexpr int SUB = 3;        // sub-tiles (128-byte k-slices) per stage: one wait, one release
+    static constexpr int STAGES = 3;     // shared-memory pipeline depth
+    static constexpr int PROD_WARPS = SUB * STAGES;  // producer warps; each loads whole sub-tiles
+    static constexpr int A_BYTES = BM * 128;
+    static constexpr int B_BYTES = NQ * 128;         // one query part of the chunk
+    static constexpr int SUBTILE_BYTES = A_BYTES + QP * B_BYTES;  // leaf rows, then the parts
+    static constexpr int STAGE_BYTES = SUB * SUBTILE_BYTES;
+    static constexpr int MMA_N = QP * NQ;            // the parts side by side
+    static constexpr int ACC_COLS = 64;              // columns per accumulator (MMA_N <= 64)
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;   // two accumulators
+    static constexpr int MMA_WARP = 4 + PROD_WARPS;  // warps 4 .. 3 + PROD_WARPS load
+    static constexpr int THREADS = (MMA_WARP + 1) * 32;
+    // shared-memory plan (offsets from a 1024-aligned base)
+    static constexpr int SM_WL = STAGES * STAGE_BYTES;            // the epilogue warps' lists [4][NQ][32]
+    static constexpr int SM_BAR = SM_WL + 4 * NQ * 32 * 8;        // full[STAGES] empty[STAGES] dfull[2] dempty[2] fin
+    static constexpr int SM_MISC = SM_BAR + (2 * STAGES + 5) * 8; // tensor-memory base, abort flag
+    static constexpr int SMEM_BYTES = SM_MISC + 16 + 1024;        // slack for aligning the base
+    // instruction descriptor: float32 D, A and B K-major, M = BM, N = MMA_N; bf16 inputs (kind::f16)
+    // or E4M3 inputs (kind::f8f6f4, format code 0)
+    static constexpr uint32_t IDESC = (1u << 4) | (FMT == LF_BF16 ? (1u << 7) | (1u << 10) : 0u) |
+                                      ((uint32_t)(MMA_N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static_assert(SUBTILE_BYTES % 1024 == 0, "sub-tiles must keep the 1024-byte swizzle alignment");
+    static_assert(MMA_N % 16 == 0 && MMA_N <= ACC_COLS, "MMA shape");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
 
 // ---------------------------------------------------------------- PTX wrappers
 
@@ -110,14 +130,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after about two seconds
 
 // Wait for the phase of `parity` to complete.  Returns false (and raises the CTA's abort flag and
-// the device status) if it did not within WAIT_NS, or if another role of the CTA aborted.
-__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// the device status) if it did not within limit_ns, or if another role of the CTA aborted.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                            uint64_t limit_ns) {
     const uint64_t t0 = globaltimer();
     for (uint32_t spin = 1;; ++spin) {
         if (mbar_test(bar, parity)) return true;
         if ((spin & 255) == 0) {
             if (*abort_flag) return false;
-            if (globaltimer() - t0 > WAIT_NS) {
+            if (globaltimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicCAS(&g_kernel_status, 0, GF_ETIMEOUT);
                 return false;
@@ -127,8 +148,9 @@ __device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, vola
     }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abort_flag);
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns) {
+    return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abort_flag, limit_ns);
 }
 
 // 16-byte global -> shared copy that reads `bytes` (0..16) bytes and zero-fills the rest
@@ -159,23 +181,39 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16 with bf16 A and B, float32 D, both K-major, M = BM, N = MMA_N.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// The MMAs of one 128-byte k-slice (four steps of 32 bytes: K = 16 bf16 or 32 E4M3 values each):
+// D (+)= A B^T, accumulating from the first unless `accumulate` is 0.  Descriptors advance 32 bytes
+// (2 in units of 16) per step.  nk < 4 issues the first nk steps only (the row's end).
+#define GF_MMA4(KIND)                                                                                          \
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.b32 p, %3, 0;\n setp.eq.b32 q, 0, 0;\n"                    \
+                 " tcgen05.mma.cta_group::1.kind::" KIND " [%0], %1, %2, %4, p;\n"                           \
+                 " tcgen05.mma.cta_group::1.kind::" KIND " [%0], %5, %6, %4, q;\n"                           \
+                 " tcgen05.mma.cta_group::1.kind::" KIND " [%0], %7, %8, %4, q;\n"                           \
+                 " tcgen05.mma.cta_group::1.kind::" KIND " [%0], %9, %10, %4, q;\n}" ::"r"(d_tmem),          \
+                 "l"(a), "l"(b), "r"(accumulate), "r"(idesc), "l"(a + 2), "l"(b + 2), "l"(a + 4), "l"(b + 4), \
+                 "l"(a + 6), "l"(b + 6)                                                                     \
+                 : "memory")
+#define GF_MMA1(KIND)                                                                                          \
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n"                                             \
+                 " tcgen05.mma.cta_group::1.kind::" KIND " [%0], %1, %2, %4, p;\n}" ::"r"(d_tmem),            \
+                 "l"(a + 2 * i), "l"(b + 2 * i), "r"(i > 0 ? 1u : accumulate), "r"(idesc)                   \
+                 : "memory")
 
-// The four MMAs of one stage (K = 64 as four steps of 16): D (+)= A B^T, accumulating from the
-// first unless `accumulate` is 0.  Descriptors advance 32 bytes (2 in units of 16) per step.
-__device__ __forceinline__ void mma_stage(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.b32 p, %3, 0;\n setp.eq.b32 q, 0, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %4, q;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %4, q;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %4, q;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(accumulate), "r"(IDESC), "l"(a + 2), "l"(b + 2), "l"(a + 4), "l"(b + 4), "l"(a + 6),
-        "l"(b + 6)
-        : "memory");
+template <int FMT>
+__device__ __forceinline__ void mma_slice(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate, int nk) {
+    constexpr uint32_t idesc = LeafCfg<FMT>::IDESC;
+    if (nk >= 4) {
+        if constexpr (FMT == LF_FP8) GF_MMA4("f8f6f4");
+        else GF_MMA4("f16");
+    } else {
+        for (int i = 0; i < nk; ++i) {
+            if constexpr (FMT == LF_FP8) GF_MMA1("f8f6f4");
+            else GF_MMA1("f16");
+        }
+    }
 }
+#undef GF_MMA4
+#undef GF_MMA1
 
 // arrive on `bar` once every tensor-core operation this thread issued so far has completed
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -281,12 +319,16 @@ struct LeafArgs {
     const int *bcnt;       // queries per bucket
     const int *boff;       // first position of each bucket in qlist
     const int *qlist;      // (query, slot) pairs q S + s grouped by bucket
-    const __nv_bfloat16 *qhi, *qlo;  // [m][ldb] query parts (bf16 screen)
+    const unsigned char *qpart;      // [QP][m][row] the query parts of the tensor-core screen:
+                                     // bf16 hi, lo ([m][ldb]) or E4M3 p0, p1, p2 ([m][ld8])
+    long long qpart_stride;          // bytes from one part to the next (m rows)
+    const float *qc;                 // [m] E4M3 parts: the scale c of part 0 (a power of two)
     const float *qf;                 // [m][ldx] the queries, rows padded (float32 kernel)
     unsigned long long *part;        // [m][S][R] keys of every (query, slot)
     unsigned long long *tau;         // [m] upper bound on each query's R-th best key
     int R;
     int S;                           // slots (leaves) per query: T, or the priority search's budget
+    unsigned long long wait_ns;      // time limit of the pipeline's mbarrier waits
 };
 
 __device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A, int w, int &t, long long &lo,
@@ -301,17 +343,22 @@ __device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A,
     nq = min(NQ, A.bcnt[u] - it.y);
 }
 
-__global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArgs A) {
+template <int FMT>
+__global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestView F, LeafArgs A) {
+    using Cfg = LeafCfg<FMT>;
+    constexpr int QP = Cfg::QP, SUB = Cfg::SUB, STAGES = Cfg::STAGES, PROD_WARPS = Cfg::PROD_WARPS;
+    constexpr int A_BYTES = Cfg::A_BYTES, B_BYTES = Cfg::B_BYTES, SUBTILE_BYTES = Cfg::SUBTILE_BYTES;
+    constexpr int STAGE_BYTES = Cfg::STAGE_BYTES, MMA_WARP = Cfg::MMA_WARP, ACC_COLS = Cfg::ACC_COLS;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned long long *wl = reinterpret_cast<unsigned long long *>(sm + SM_WL);
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm + SM_BAR);
+    unsigned long long *wl = reinterpret_cast<unsigned long long *>(sm + Cfg::SM_WL);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + Cfg::SM_BAR);
     uint64_t *empty = full + STAGES;
     uint64_t *dfull = empty + STAGES;
     uint64_t *dempty = dfull + 2;
     uint64_t *fin = dempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + SM_MISC);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + SM_MISC + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Cfg::SM_MISC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + Cfg::SM_MISC + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -329,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     }
     if (warp == MMA_WARP) {  // the MMA warp owns the tensor memory
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "n"(TMEM_COLS)
+                     "n"(Cfg::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -338,12 +385,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const int item_lo = *A.item_lo, item_hi = *A.item_hi;
-    const int KC = (F.d + SUB * BK - 1) / (SUB * BK);  // stages per row tile
-    const uint32_t stage0 = smem_u32(sm + SM_STAGES);
+    // bytes of a row that hold values, and of a padded row
+    const int row_bytes = F.d * Cfg::ESZ;
+    const int pitch = FMT == LF_FP8 ? F.ld8 : F.ldb * 2;
+    const unsigned char *xrows = FMT == LF_FP8 ? F.x8 : reinterpret_cast<const unsigned char *>(F.xb);
+    const int KC = (row_bytes + SUB * 128 - 1) / (SUB * 128);  // stages per row tile
+    const uint32_t stage0 = smem_u32(sm);
 
     if (warp >= 4 && warp < MMA_WARP) {
         // ------------------------------------------------ producers: leaf rows and query parts
-        // Sub-tile h = SUB g + u of the CTA's stream (stage g, k-step u) belongs to producer warp
+        // Sub-tile h = SUB g + u of the CTA's stream (stage g, k-slice u) belongs to producer warp
         // h % PROD_WARPS.  The warp copies the whole sub-tile (lane: one 16-byte column chunk of
         // every fourth row), waits for its own copies, makes them visible to the tensor cores and
         // arrives on the stage's full barrier: no sub-tile waits for another one's copies.
@@ -377,30 +428,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                         ids[i] = gr < rows ? __ldg(F.perm + (size_t)t * F.n + lo + gr) : -1;
                     }
                 }
-                if (!mbar_wait(empty + s, ((g / STAGES) & 1) ^ 1, abort_flag)) { ok = false; break; }
-                const int kcol = (kc * SUB + u) * BK;
-                if (kcol >= F.d) {  // past the row: nothing to load, the MMA skips this sub-tile
+                if (!mbar_wait(empty + s, ((g / STAGES) & 1) ^ 1, abort_flag, A.wait_ns)) { ok = false; break; }
+                const int kbyte = (kc * SUB + u) * 128;
+                if (kbyte >= row_bytes) {  // past the row: nothing to load, the MMA skips this sub-tile
                     mbar_arrive(full + s);
                     continue;
                 }
-                const int col = kcol + c * 8;
-                const int nb = max(0, min(16, (F.d - col) * 2));
+                const int col = kbyte + c * 16;
+                const int nb = max(0, min(16, row_bytes - col));
                 const uint32_t sa = stage0 + s * STAGE_BYTES + u * SUBTILE_BYTES;
 #pragma unroll
                 for (int i = 0; i < BM / 4; ++i) {
                     const int r = r0 + 4 * i;
                     const bool live = ids[i] >= 0 && nb > 0;
-                    const __nv_bfloat16 *src = live ? F.xb + (size_t)ids[i] * F.ldb + col : F.xb;
+                    const unsigned char *src = live ? xrows + (size_t)ids[i] * pitch + col : xrows;
                     cp_async16(sa + r * 128 + ((c ^ (r & 7)) << 4), src, live ? nb : 0);
                 }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const __nv_bfloat16 *qb = h ? A.qlo : A.qhi;
+                for (int h = 0; h < QP; ++h) {
+                    const unsigned char *qb = A.qpart + h * A.qpart_stride;
 #pragma unroll
                     for (int i = 0; i < NQ / 4; ++i) {
                         const int j = r0 + 4 * i;
                         const bool live = qid[i] >= 0 && nb > 0;
-                        const __nv_bfloat16 *src = live ? qb + (size_t)qid[i] * F.ldb + col : qb;
+                        const unsigned char *src = live ? qb + (size_t)qid[i] * pitch + col : qb;
                         cp_async16(sa + A_BYTES + h * B_BYTES + j * 128 + ((c ^ (j & 7)) << 4), src, live ? nb : 0);
                     }
                 }
@@ -418,7 +469,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
             uint32_t tile = 0, s = 0, ph = 0;  // next stage slot and the parity of its fill
             bool ok = true;
             const uint64_t da0 = sdesc_sw128(stage0);            // stage 0's leaf rows
-            const uint64_t db0 = sdesc_sw128(stage0 + A_BYTES);  // stage 0's query rows: hi, then lo
+            const uint64_t db0 = sdesc_sw128(stage0 + A_BYTES);  // stage 0's query parts
             for (int w = item_lo + blockIdx.x; w < item_hi && ok; w += gridDim.x) {
                 int t, rows, q0pos, nq;
                 long long lo;
@@ -426,16 +477,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                 const int MT = (rows + BM - 1) / BM;
                 for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
                     const uint32_t buf = tile & 1;
-                    if (!mbar_wait(dempty + buf, ((tile >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(dempty + buf, ((tile >> 1) & 1) ^ 1, abort_flag, A.wait_ns)) { ok = false; break; }
                     tc_fence_after();  // the epilogue's reads of this accumulator are done
-                    const uint32_t d_tmem = tmem_base + buf * MMA_N;
+                    const uint32_t d_tmem = tmem_base + buf * ACC_COLS;
                     for (int kc = 0; kc < KC; ++kc) {
-                        if (!mbar_wait(full + s, ph, abort_flag)) { ok = false; break; }
+                        if (!mbar_wait(full + s, ph, abort_flag, A.wait_ns)) { ok = false; break; }
 #pragma unroll
                         for (int u = 0; u < SUB; ++u) {
-                            if ((kc * SUB + u) * BK >= F.d) break;
+                            const int kbyte = (kc * SUB + u) * 128;
+                            if (kbyte >= row_bytes) break;
                             const uint64_t off = (uint64_t)((s * STAGE_BYTES + u * SUBTILE_BYTES) >> 4);
-                            mma_stage(d_tmem, da0 + off, db0 + off, (kc | u) != 0);
+                            mma_slice<FMT>(d_tmem, da0 + off, db0 + off, (kc | u) != 0, (row_bytes - kbyte + 31) >> 5);
                         }
                         mma_commit(empty + s);
                         if (++s == STAGES) { s = 0; ph ^= 1; }
@@ -444,10 +496,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
                     mma_commit(dfull + buf);
                 }
             }
-            // every issued operation has completed before the tensor memory is freed
+            // every issued operation has completed before the tensor memory is freed (the full
+            // limit, whatever the pipeline waits were given)
             mma_commit(fin);
             volatile int no_abort = 0;
-            mbar_wait_slow(fin, 0, &no_abort);
+            mbar_wait_slow(fin, 0, &no_abort, WAIT_NS);
         }
         __syncwarp();
     } else {
@@ -467,37 +520,49 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
             unsigned long long lst[NQ];
 #pragma unroll
             for (int j = 0; j < NQ; ++j) lst[j] = KEY_NONE;
-            // lane j: query j of the chunk and its bound
+            // lane j: query j of the chunk, its bound and (E4M3 parts) the scale of its part 0
             const int my_qid = lane < nq ? A.qlist[q0pos + lane] / A.S : 0;
             const unsigned long long my_tau = lane < nq ? __ldcg(A.tau + my_qid) : KEY_NONE;
+            const float my_c = FMT == LF_FP8 && lane < nq ? __ldg(A.qc + my_qid) : 1.f;
             const int MT = (rows + BM - 1) / BM;
             for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
                 const int r = mt * BM + et;
                 const bool valid = r < rows;
                 const int id = valid ? __ldg(F.perm + (size_t)t * F.n + lo + r) : 0;
-                const float xn = valid ? __ldg(F.xbn + id) : 0.f;
+                // |x~|^2 and the factor of x~.q in the score: -2 (bf16), -2 s_x (E4M3 codes)
+                const float xn = valid ? __ldg(FMT == LF_FP8 ? F.x8n + id : F.xbn + id) : 0.f;
+                const float kx = FMT == LF_FP8 ? (valid ? -2.f * __ldg(F.scale8 + id) : 0.f) : -2.f;
                 const uint32_t buf = tile & 1;
-                if (!mbar_wait(dfull + buf, (tile >> 1) & 1, abort_flag)) ok = false;
+                if (!mbar_wait(dfull + buf, (tile >> 1) & 1, abort_flag, A.wait_ns)) ok = false;
                 ok = __all_sync(FULL, ok);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t ta = tmem_base + ((uint32_t)(warp * 32) << 16) + buf * MMA_N;
-                float v[NQ];  // x~ . (q_hi + q_lo) of the lane's row for every query of the chunk
+                const uint32_t ta = tmem_base + ((uint32_t)(warp * 32) << 16) + buf * ACC_COLS;
+                float v[NQ];  // x~ . q~ of the lane's row for every query of the chunk (codes for E4M3)
+                {
+                    uint32_t acc[QP][16];
 #pragma unroll
-                for (int h = 0; h < NQ / 16; ++h) {
-                    uint32_t hi[16], lo16[16];
-                    tmem_ld16(ta + 16 * h, hi);
-                    tmem_ld16(ta + NQ + 16 * h, lo16);
+                    for (int p = 0; p < QP; ++p) tmem_ld16(ta + p * NQ, acc[p]);
                     tmem_wait();
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[16 * h + i] = __uint_as_float(hi[i]) + __uint_as_float(lo16[i]);
+                    for (int i = 0; i < 16; ++i) {
+                        if (FMT == LF_FP8)  // p0 + p1 / 16 + p2 / 256 (exact scalings)
+                            v[i] = __uint_as_float(acc[0][i]) +
+                                   fmaf(__uint_as_float(acc[2][i]), 1.f / 16.f, __uint_as_float(acc[1][i])) *
+                                       (1.f / 16.f);
+                        else
+                            v[i] = __uint_as_float(acc[0][i]) + __uint_as_float(acc[1][i]);
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(dempty + buf);
 #pragma unroll
                 for (int j = 0; j < NQ; ++j) {
                     if (j < nq) {
-                        const float s = fmaf(-2.f, v[j], xn);
+                        // screened score |x~|^2 - 2 x~.q~; for E4M3 -2 s_x c is a power-of-two
+                        // multiple of s_x, so the product is exact
+                        const float kj = FMT == LF_FP8 ? kx * __shfl_sync(FULL, my_c, j) : kx;
+                        const float s = fmaf(kj, v[j], xn);
                         const unsigned long long key =
                             valid ? (((unsigned long long)ord_f32(s) << 32) | (unsigned)id) : KEY_NONE;
                         const unsigned long long thr =
@@ -529,7 +594,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leaf_score(ForestView F, LeafArg
     __syncthreads();
     tc_fence_after();
     if (warp == MMA_WARP)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(Cfg::TMEM_COLS)
                      : "memory");
 }
 
@@ -807,6 +872,47 @@ __global__ void k_qsplit(const float *__restrict__ Q, long long m, int d, int ld
     }
 }
 
+// q -> three E4M3 parts for the kind::f8f6f4 screen, one warp per query.  c = the smallest power of
+// two with max_j |q_j| / c <= 448 (1 for a zero query); then part p holds e4m3_rne(r_p / c_p) with
+// c_p = c / 16^p, r_0 = q and r_{p+1} = r_p - c_p p_p (exact in float32: c_p p_p holds the leading
+// bits of r_p).  Rounding to E4M3 leaves at most 2^-4 of a value, or half a subnormal step
+// (2^-10 c_p), so |r_{p+1}| <= max(2^-4 |r_p|, 2^-10 c_p): every part's values stay within +-448,
+// and q = c (p_0 + p_1 / 16 + p_2 / 256) + e with |e_j| <= 2^-12 |q_j| + 2^-18 c.  Zero in the row
+// padding.
+__global__ void k_qsplit8(const float *__restrict__ Q, long long m, int d, int ld8, unsigned char *parts,
+                          long long part_stride, float *qc) {
+    const int lane = threadIdx.x & 31;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m;
+         i += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const float *q = Q + i * d;
+        float a = 0.f;
+        for (int j = lane; j < d; j += 32) a = fmaxf(a, fabsf(q[j]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(FULL, a, o));
+        // the smallest power of two c with a / c <= 448
+        float c = 1.f;
+        if (a > 0.f) {
+            int e;
+            frexpf(a / 448.f, &e);  // a / 448 = f 2^e, f in [0.5, 1)
+            c = ldexpf(1.f, e);
+            if (a / ldexpf(1.f, e - 1) <= 448.f) c = ldexpf(1.f, e - 1);
+        }
+        if (lane == 0) qc[i] = c;
+        for (int j = lane; j < ld8; j += 32) {
+            float r = j < d ? q[j] : 0.f;
+            float cp = c;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(r / cp, __NV_SATFINITE, __NV_E4M3);
+                parts[p * part_stride + i * ld8 + j] = (unsigned char)b;
+                const __half_raw hv = __nv_cvt_fp8_to_halfraw(b, __NV_E4M3);
+                r = r - cp * __half2float(*reinterpret_cast<const __half *>(&hv));
+                cp *= (1.f / 16.f);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- merge + rerank
 
 // Per query: the keys of its S lists of R at or below its final bound tau_q (every key of the
@@ -838,7 +944,9 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
         // come together, its best score first
         for (int i = threadIdx.x; i < TR; i += blockDim.x) {
             const unsigned long long key = part[qi * TR + i];
-            if (key != KEY_NONE && key <= tq) a[atomicAdd(&nkeep, 1)] = (key << 32) | (key >> 32);
+            // (an id outside [0, n) is a list no scoring CTA wrote: its launch gave up a wait)
+            if (key != KEY_NONE && key <= tq && (key & 0xffffffffull) < (unsigned long long)F.n)
+                a[atomicAdd(&nkeep, 1)] = (key << 32) | (key >> 32);
         }
         __syncthreads();
         const int n = nkeep;
@@ -882,7 +990,8 @@ size_t merge_smem(const gf_forest *F, int S, int R) {
 
 struct LeafWorkspace {
     size_t bcnt, bfill, kcnt, kfill, zero_end;  // counters, zeroed by every call
-    size_t boff, koff, leaf, pn, qlist, items, qhi, qlo, part, tau, total;
+    size_t boff, koff, leaf, pn, qlist, items, qpart, qc, part, tau, total;
+    size_t qpart_stride;  // bytes per query part ([m] rows)
 };
 
 // S: leaves per query (T, or the priority search's budget)
@@ -904,8 +1013,11 @@ LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int S, int R, int or
     W.pn = o; o = al(o + (size_t)m * 4);
     W.qlist = o; o = al(o + pairs * 4);
     W.items = o; o = al(o + pairs * 8);
-    W.qhi = o; o = al(o + (size_t)m * F->ldb * 2);
-    W.qlo = o; o = al(o + (size_t)m * F->ldb * 2);
+    // the query parts: bf16 hi and lo [m][ldb], or three E4M3 parts [m][ld8] (and their scales),
+    // or the float32 kernel's padded copy [m][ldx]; room for the largest
+    W.qpart_stride = std::max((size_t)m * F->ldb * 2, al((size_t)m * F->ld8));
+    W.qpart = o; o = al(o + std::max(3 * W.qpart_stride, (size_t)m * F->ldx * 4));
+    W.qc = o; o = al(o + (size_t)m * 4);
     W.part = o; o = al(o + pairs * R * 8);
     W.tau = o; o = al(o + (size_t)m * 8);
     W.total = o;
@@ -918,8 +1030,9 @@ int order_of(int order) { return order == GF_ORDER_GIVEN ? GF_ORDER_GIVEN : GF_O
 
 const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R,
                                 const QueryExtra &x) {
-    if (precision != GF_BF16_RERANK && precision != GF_FP32) return "the leaf-major path runs float32 or the bf16 screen";
+    if (precision < GF_FP32 || precision > GF_FP8_RERANK) return "unknown precision";
     if (precision == GF_BF16_RERANK && (!F->xb || !F->xbn)) return "the forest has no bf16 copy";
+    if (precision == GF_FP8_RERANK && (!F->x8 || !F->x8n)) return "the forest has no fp8 copy";
     if (x.ncand_out) return "candidate counts are reported by the streaming kernel only";
     const int S = x.leaf_budget > 0 ? x.leaf_budget : F->T;  // leaves per query
     if (x.leaf_budget > 0 && ((unsigned long long)F->T << F->L) > 0xffffffffull)
@@ -957,7 +1070,7 @@ int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision
 
 int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision, int32_t R,
                    int32_t order, int32_t leaf_budget, cudaStream_t st, int64_t *ids, float *dists,
-                   void *workspace, int64_t workspace_bytes) {
+                   void *workspace, int64_t workspace_bytes, cudaEvent_t *events) {
     order = order_of(order);
     const bool f32 = precision == GF_FP32;
     if (f32) R = k;  // the exact distances: the k best of every (query, leaf) suffice
@@ -986,7 +1099,8 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     int *boff = (int *)(ws + W.boff), *koff = (int *)(ws + W.koff);
     int *leaf = (int *)(ws + W.leaf), *pn = (int *)(ws + W.pn), *qlist = (int *)(ws + W.qlist);
     int2 *items = (int2 *)(ws + W.items);
-    __nv_bfloat16 *qhi = (__nv_bfloat16 *)(ws + W.qhi), *qlo = (__nv_bfloat16 *)(ws + W.qlo);
+    unsigned char *qpart = (unsigned char *)(ws + W.qpart);
+    float *qc = (float *)(ws + W.qc);
     unsigned long long *part = (unsigned long long *)(ws + W.part);
     unsigned long long *tau = (unsigned long long *)(ws + W.tau);
     const int nb = F->T << F->L;
@@ -1016,35 +1130,50 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, P, locality, kcnt);
     k_scan<<<1, 1024, 0, st>>>(kcnt, nk, koff);
     k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, P, locality, koff, kfill, items);
-    // float32: the padded query copy takes the place of the two bf16 parts (as large together)
-    float *qf = (float *)(ws + W.qhi);
+    // the queries as the scoring kernel reads them: the float32 kernel's padded copy, the bf16 parts
+    // hi and lo, or the three E4M3 parts and their scales
+    float *qf = (float *)qpart;
+    const bool f8 = precision == GF_FP8_RERANK;
     if (f32) k_qpad<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldx, qf);
-    else k_qsplit<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldb, qhi, qlo);
+    else if (f8) k_qsplit8<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ld8, qpart, (long long)W.qpart_stride, qc);
+    else k_qsplit<<<F->num_sms * 8, 256, 0, st>>>(Q, m, F->d, F->ldb, (__nv_bfloat16 *)qpart,
+                                                  (__nv_bfloat16 *)(qpart + W.qpart_stride));
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major regrouping");
 
     e = f32 ? cudaFuncSetAttribute(k_leaf_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, f32k::SMEM)
-            : cudaFuncSetAttribute(k_leaf_score, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        : f8 ? cudaFuncSetAttribute(k_leaf_score<LF_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    LeafCfg<LF_FP8>::SMEM_BYTES)
+             : cudaFuncSetAttribute(k_leaf_score<LF_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    LeafCfg<LF_BF16>::SMEM_BYTES);
     if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(leaf-major scoring)");
     LeafArgs A;
     A.items = items;
     A.bcnt = bcnt;
     A.boff = boff;
     A.qlist = qlist;
-    A.qhi = qhi;
-    A.qlo = qlo;
+    A.qpart = qpart;
+    A.qpart_stride = (long long)W.qpart_stride;
+    A.qc = qc;
     A.qf = qf;
     A.part = part;
     A.tau = tau;
     A.R = R;
     A.S = S;
+    const unsigned long long wl = g_wait_limit_ns.load();
+    A.wait_ns = wl ? wl : WAIT_NS;
     // the chunks of tree 0 (keys below 2^L) set every query's bound; then all the others
+    if (events && (e = cudaEventRecord(events[0], st)) != cudaSuccess) return fail(e, "cudaEventRecord");
     for (int wave = 0; wave < 2; ++wave) {
         A.item_lo = wave == 0 ? koff : koff + (1 << F->L);
         A.item_hi = wave == 0 ? koff + (1 << F->L) : koff + nk;
         if (f32) k_leaf_f32<<<F->num_sms * f32k::CTAS_PER_SM, f32k::THREADS, f32k::SMEM, st>>>(view_of(F), A);
-        else k_leaf_score<<<F->num_sms, THREADS, SMEM_BYTES, st>>>(view_of(F), A);
+        else if (f8)
+            k_leaf_score<LF_FP8><<<F->num_sms, LeafCfg<LF_FP8>::THREADS, LeafCfg<LF_FP8>::SMEM_BYTES, st>>>(view_of(F), A);
+        else
+            k_leaf_score<LF_BF16><<<F->num_sms, LeafCfg<LF_BF16>::THREADS, LeafCfg<LF_BF16>::SMEM_BYTES, st>>>(view_of(F), A);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major scoring launch");
+    if (events && (e = cudaEventRecord(events[1], st)) != cudaSuccess) return fail(e, "cudaEventRecord");
 
     const size_t msmem = merge_smem(F, S, R);
     const unsigned mg = (unsigned)std::min<long long>(m, (long long)F->num_sms * 16);
@@ -1063,6 +1192,11 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     // a caller's workspace is handed back all zero, as the streaming kernel expects it
     if (!own && (e = cudaMemsetAsync(ws, 0, W.total, st)) != cudaSuccess) return fail(e, "workspace clear");
     if (own) cudaFreeAsync(ws, st);
+    return GF_OK;
+}
+
+extern "C" int gf_debug_set_wait_limit(uint64_t ns) {
+    g_wait_limit_ns.store(ns);
     return GF_OK;
 }
 

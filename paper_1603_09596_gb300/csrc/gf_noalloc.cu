@@ -46,6 +46,7 @@ extern "C" int gf_query_noalloc(const gf_forest *F, const float *Q, int64_t m, i
     if (m < 0 || k < 1) return gf_fail(GF_EINVAL, "gf_query_noalloc: bad sizes");
     if (m == 0) return GF_OK;
     if (!Q || !ids || !dists) return gf_fail(GF_EINVAL, "gf_query_noalloc: null pointer");
+    if (precision < 0 || precision > 2) return gf_fail(GF_EINVAL, "gf_query_noalloc: unknown precision %d", precision);
     const int64_t words = (F->n + 31) / 32;
     const int64_t per_cta = words * 4;
     const int64_t max_ctas = (int64_t)GF_NOALLOC_SCRATCH_BYTES / per_cta;
@@ -58,12 +59,6 @@ extern "C" int gf_query_noalloc(const gf_forest *F, const float *Q, int64_t m, i
     int r = scratch_on_current_device(&scratch);
     if (r) return r;
     cudaStream_t st = (cudaStream_t)stream;
-    // Queries go in chunks of at most max_ctas rows, so no launch uses more CTAs -- and bitmaps --
-    // than the array holds.  The part a launch uses is cleared first: the array keeps whatever the
-    // last call left in it.
-    const int64_t chunk = max_ctas;
-    const int64_t used = std::min<int64_t>(chunk, m) * per_cta;
-    GF_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)used, st));
     gf_query_opts o;
     gf_query_opts_default(&o);
     o.precision = precision;
@@ -72,6 +67,31 @@ extern "C" int gf_query_noalloc(const gf_forest *F, const float *Q, int64_t m, i
     o.algo = GF_ALGO_STREAM;
     o.workspace = scratch;
     o.workspace_bytes = GF_NOALLOC_SCRATCH_BYTES;
+    // The queries go in launches of `chunk` rows: the longest whose whole scratch layout -- the
+    // launch's bitmaps and, when its CTAs take the queries in locality order, 12 bytes a query --
+    // fits in the array.  The layout grows with the rows of a launch, so a bisection finds it.
+    auto need = [&](int64_t rows, int64_t *bytes) { return gf_query_workspace_size(F, rows, &o, bytes); };
+    int64_t bytes = 0;
+    int64_t chunk = m;
+    if ((r = need(m, &bytes))) return r;
+    if (bytes > GF_NOALLOC_SCRATCH_BYTES) {
+        int64_t lo = 1, hi = m;  // need(lo) fits, need(hi) does not
+        while (hi - lo > 1) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if ((r = need(mid, &bytes))) return r;
+            (bytes <= GF_NOALLOC_SCRATCH_BYTES ? lo : hi) = mid;
+        }
+        chunk = lo;
+    }
+    // Only the bitmaps must start at zero (the locality keys are written before they are read).
+    // They are the first grid * per_cta bytes, grid being at most the CTA count the size bound
+    // above assumed for a launch of `chunk` rows.  The array keeps whatever the last call left in
+    // it, e.g. another forest's keys, so they are cleared here.
+    long long grid = 0;
+    if ((r = gf_stream_grid(F, chunk, std::min(8, F->tune_warps[precision]), F->tune_ctas[precision], precision, 1,
+                            rerank_R > 0 ? rerank_R : F->tune_R[precision], &grid)))
+        return r;
+    GF_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)(grid * per_cta), st));
     for (int64_t off = 0; off < m; off += chunk) {
         const int64_t mc = std::min<int64_t>(chunk, m - off);
         r = gf_query_ex(F, Q + off * F->d, mc, k, &o, ids + off * k, dists + off * k);

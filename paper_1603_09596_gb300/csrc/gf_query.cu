@@ -303,24 +303,36 @@ __global__ void k_score_topk(ForestView F, const float *__restrict__ Q, long lon
     }
 }
 
-// Screened distance of every candidate (no selection), for checking the screen arithmetic.
+// Screened distance of every candidate (no selection), for checking the screen arithmetic.  The
+// candidates go through shared memory in blocks of SCORE_BLOCK, so any candidate count fits.
+constexpr int SCORE_BLOCK = 2048;
+
+__host__ __device__ inline size_t score_all_smem(int d) {
+    return (size_t)SCORE_BLOCK * 8 + (size_t)ldq_of(d) * 4 + (size_t)SCORE_BLOCK * 4;
+}
+
 template <int PREC, int NC>
 __global__ void k_score_all(ForestView F, const float *__restrict__ Q, long long m,
                             const int *__restrict__ cand, const int *__restrict__ ncand, int stride,
                             float *out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem s = carve(smem_raw, F.d, F.T, F.cand_cap);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem_raw);
+    float *qs = reinterpret_cast<float *>(keys + SCORE_BLOCK);
+    int *u = reinterpret_cast<int *>(qs + ldq_of(F.d));
     for (long long i = blockIdx.x; i < m; i += gridDim.x) {
-        load_query(Q + i * F.d, F.d, s.qs);
-        const int C = min(max(ncand[i], 0), min(stride, F.cand_cap));
-        for (int j = threadIdx.x; j < C; j += blockDim.x) s.u[j] = cand[(size_t)i * stride + j];
-        __syncthreads();
-        score_rows<PREC, NC>(F, s.qs, s.u, C, s.keys);
-        __syncthreads();
-        for (int j = threadIdx.x; j < C; j += blockDim.x)
-            out[(size_t)i * stride + j] = s.keys[j] == KEY_NONE ? __int_as_float(0x7fc00000)
-                                                                 : __uint_as_float((unsigned)(s.keys[j] >> 32));
-        __syncthreads();
+        load_query(Q + i * F.d, F.d, qs);
+        const int C = min(max(ncand[i], 0), stride);
+        for (int b0 = 0; b0 < C; b0 += SCORE_BLOCK) {
+            const int nb = min(SCORE_BLOCK, C - b0);
+            for (int j = threadIdx.x; j < nb; j += blockDim.x) u[j] = cand[(size_t)i * stride + b0 + j];
+            __syncthreads();
+            score_rows<PREC, NC>(F, qs, u, nb, keys);
+            __syncthreads();
+            for (int j = threadIdx.x; j < nb; j += blockDim.x)
+                out[(size_t)i * stride + b0 + j] = keys[j] == KEY_NONE ? __int_as_float(0x7fc00000)
+                                                                        : __uint_as_float((unsigned)(keys[j] >> 32));
+            __syncthreads();
+        }
     }
 }
 
@@ -371,7 +383,7 @@ __global__ void k_query_fused(ForestView F, const float *__restrict__ Q, long lo
 //   rescores its R best in float32) and the query's bits are cleared, so the bitmap is all zero
 //   between queries.
 
-constexpr int LIST = 2048;  // positions per phase
+constexpr int LIST = GF_MAX_SHORTLIST;  // positions per phase; also the longest k or R
 
 struct StreamLayout {
     size_t buf, list, qs, pref, lbase, lcnt, lpos, hist, wtmp, sh, total;
@@ -642,7 +654,7 @@ int check_smem(const gf_forest *F, size_t smem) {
 
 template <int PREC, int NC, int NCF>
 int launch_fused(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t R, int warps,
-                 int ctas_per_sm, cudaStream_t st, int64_t *ids, float *dists) {
+                 int ctas_per_sm, cudaStream_t st, int64_t *ids, float *dists, const QueryExtra &x) {
     const size_t smem = smem_bytes(F->d, F->T, F->cand_cap);
     int r = check_smem(F, smem);
     if (r) return r;
@@ -661,8 +673,10 @@ int launch_fused(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32
     }
     long long grid = (long long)F->num_sms * ctas_per_sm;
     if (grid > m) grid = m;
+    GF_CUDA_TRY(gf_record(x, 0, st));
     kern<<<(unsigned)grid, threads, smem, st>>>(view_of(F), Q, m, k, R, (long long *)ids, dists);
     GF_CUDA_TRY(cudaGetLastError());
+    GF_CUDA_TRY(gf_record(x, 1, st));
     return GF_OK;
 }
 
@@ -770,10 +784,12 @@ int launch_stream_g(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         }
         k_order_sort<<<(unsigned)chunks, 1024, osmem, st>>>(m, okeys, order);
     }
+    cudaError_t e = gf_record(x, 0, st);
     kern<<<(unsigned)grid, threads, smem, st>>>(view_of(F), Q, m, k, R, buf_len, bitmaps, nwords, order,
                                                leaf_list, nleaf_list, nl_max, (long long *)ids, dists,
                                                x.ncand_out);
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = gf_record(x, 1, st);
     if (own) cudaFreeAsync(bitmaps, st);
     if (e != cudaSuccess) return gf_cuda_fail(e, "k_query_stream launch");
     return GF_OK;
@@ -826,7 +842,7 @@ int dispatch_prec(const gf_forest *F, const float *Q, int64_t m, int32_t k, int3
         return gf_fail(GF_EINVAL, "candidate counts are reported by the streaming kernel only");
 #define GF_CASE(A, B)                                                                              \
     if (nc == A && ncf == B)                                                                       \
-        return algo == GF_ALGO_SORT ? launch_fused<PREC, A, B>(F, Q, m, k, R, warps, cps, st, ids, dists) \
+        return algo == GF_ALGO_SORT ? launch_fused<PREC, A, B>(F, Q, m, k, R, warps, cps, st, ids, dists, x) \
                                     : launch_stream<PREC, A, B>(F, Q, m, k, R, warps, cps, st, ids, dists, x);
     if (PREC == P_F32) {
         GF_CASE(1, 1) GF_CASE(2, 2) GF_CASE(4, 4) GF_CASE(8, 8) GF_CASE(0, 0)
@@ -848,7 +864,7 @@ int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         const char *why = gf_leaf_unsupported(F, m, k, precision, R, x);
         if (why) return gf_fail(GF_EUNSUPPORTED, "GF_ALGO_LEAF: %s", why);
         return gf_launch_leaf(F, Q, m, k, precision, R, x.order, x.leaf_budget, st, ids, dists, x.workspace,
-                              x.workspace_bytes);
+                              x.workspace_bytes, x.events);
     }
     switch (precision) {
         case GF_FP32: return dispatch_prec<P_F32>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x);
@@ -940,7 +956,7 @@ extern "C" int gf_score_screened(const gf_forest *F, const float *Q, int64_t m, 
     if (precision == GF_BF16_RERANK && !F->xb) return gf_fail(GF_EINVAL, "no bf16 copy");
     if (precision == GF_FP8_RERANK && !F->x8) return gf_fail(GF_EINVAL, "no fp8 copy");
     if (precision < 0 || precision > 2) return gf_fail(GF_EINVAL, "unknown precision %d", precision);
-    const size_t smem = smem_bytes(F->d, F->T, F->cand_cap);
+    const size_t smem = score_all_smem(F->d);
     int r = check_smem(F, smem);
     if (r) return r;
     const long long grid = m < (long long)F->num_sms * 4 ? m : (long long)F->num_sms * 4;

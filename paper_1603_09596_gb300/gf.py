@@ -39,7 +39,8 @@ class QueryOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rerank_R", C.c_int32), ("warps_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("stream", C.c_void_p), ("algo", C.c_int32),
                 ("rows_in_flight", C.c_int32), ("workspace", C.c_void_p), ("workspace_bytes", C.c_int64),
-                ("ncand_out", C.c_void_p), ("order", C.c_int32), ("checks", C.c_int32), ("eps", C.c_double)]
+                ("ncand_out", C.c_void_p), ("order", C.c_int32), ("checks", C.c_int32), ("eps", C.c_double),
+                ("events", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -105,6 +106,8 @@ def lib() -> C.CDLL:
             "gf_server_run_poisson": ([P, P, P, C.c_double, C.c_double, i32, u64, i32, P], i32),
             "gf_server_destroy": ([P], i32),
             "gf_kernel_status": ([P], i32),
+            "gf_debug_fail_alloc": ([i32], i32),
+            "gf_debug_set_wait_limit": ([u64], i32),
             "gf_last_error": ([], C.c_char_p),
             "gf_version": ([], i32),
             "gf_rand_params_default": ([P], None),
@@ -261,8 +264,9 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
              warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None, algo: int = GF_ALGO_AUTO,
              workspace: torch.Tensor | None = None, ncand_out: torch.Tensor | None = None,
              rows_in_flight: int = 0, order: int = GF_ORDER_AUTO, checks: int = 0, eps: float = 0.0,
-             out: tuple[torch.Tensor, torch.Tensor] | None = None):
-    """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k])."""
+             out: tuple[torch.Tensor, torch.Tensor] | None = None, events=None):
+    """k nearest neighbours of the rows of Q: (ids int64 [m, k], dists float32 [m, k]).  events: two
+    torch.cuda.Event the query records just before and after its scoring kernel's launches."""
     qp = _dptr(Q, torch.float32, "Q")
     m = Q.shape[0]
     if out is None:
@@ -272,6 +276,14 @@ def gf_query(F: Forest, Q: torch.Tensor, k: int, precision: int = GF_FP32, reran
         ids, dists = out
     o = _opts(precision, rerank_R, warps_per_cta, ctas_per_sm, stream, algo, workspace, ncand_out,
               rows_in_flight, order, checks, eps)
+    if events is not None:
+        raw = []
+        for ev in events:
+            if not ev.cuda_event:  # torch creates an event at its first record
+                ev.record(stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.current_stream())
+            raw.append(ev.cuda_event)
+        handles = (C.c_void_p * 2)(*raw)
+        o.events = C.cast(handles, C.c_void_p)
     _check(lib().gf_query_ex(F.handle, qp, m, k, C.byref(o),
                              _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists")))
     return ids, dists
@@ -421,6 +433,18 @@ def gf_kernel_status() -> int:
     v = C.c_int32(0)
     _check(lib().gf_kernel_status(C.byref(v)))
     return v.value
+
+
+def gf_debug_fail_alloc(after: int) -> None:
+    """Failure injection for tests: the (after + 1)-th library device allocation from now fails
+    with GF_ENOMEM (once); after < 0 disarms."""
+    _check(lib().gf_debug_fail_alloc(after))
+
+
+def gf_debug_set_wait_limit(ns: int) -> None:
+    """Failure injection for tests: time limit (ns, 0 = default) of the tensor-core scoring
+    kernel's pipeline waits; a short one makes them run out (GF_ETIMEOUT in gf_kernel_status)."""
+    _check(lib().gf_debug_set_wait_limit(ns))
 
 
 def gf_version() -> int:

@@ -144,6 +144,10 @@ def _mutations(small):
     nn = (1 << F.L) - 1
     bad_tuning = [row[:] for row in DEFAULT_TUNING]
     bad_tuning[3][1] = 3   # rows in flight must be 0, 2 or 4
+    many_ctas = [row[:] for row in DEFAULT_TUNING]
+    many_ctas[1][0] = 33   # an SM runs at most 32 CTAs
+    long_list = [row[:] for row in DEFAULT_TUNING]
+    long_list[2][2] = 2049  # the streaming kernel keeps at most 2048 keys per query
     flip = bytearray(good)
     flip[HEADER + len(good[HEADER:]) // 2] ^= 0x10
     w = np.frombuffer(good[HEADER:], "<u4").copy()
@@ -160,6 +164,8 @@ def _mutations(small):
         "depth": encode(F.n, F.d, F.T, F.leaf_size + 100, F.L, F.split_dim, F.split_val, F.perm, X),
         "flags": forest_blob(small, flags=8),
         "tuning": forest_blob(small, tuning=bad_tuning),
+        "tuning_ctas": forest_blob(small, tuning=many_ctas),
+        "tuning_shortlist": forest_blob(small, tuning=long_list),
         "payload_size": forest_blob(small, payload_bytes=len(good) - HEADER + 4),
         "truncated": good[:-4],
         "trailing": good + b"\0\0\0\0",
@@ -173,7 +179,7 @@ def _mutations(small):
 
 
 @pytest.mark.parametrize("kind", ["empty", "short_header", "magic", "version", "byte_order", "depth", "flags",
-                                  "tuning", "payload_size", "truncated", "trailing", "bit_flip",
+                                  "tuning", "tuning_ctas", "tuning_shortlist", "payload_size", "truncated", "trailing", "bit_flip",
                                   "swapped_words", "checksum", "header_field", "zero_trees"])
 def test_malformed_file_is_eio(gf, small, tmp_path, kind):
     p = tmp_path / f"{kind}.gff"

@@ -1,11 +1,13 @@
 """The leaf-major batched path (GF_ALGO_LEAF) against the CPU oracle's screened search.
 
 The forest is built by the oracle and imported, so both sides search the same trees.  The oracle's
-bf16 screen ranks the candidate union of every query by the float64 distance to the bf16-rounded
-points, keeps the R best and reranks them exactly; the GPU screen ranks the same union by
-|x~|^2 - 2 x~.q on the tensor cores.  As for the other screened kernels: every reported id must be a
-candidate reported with its float32 distance (1e-5 relative), and a row may differ from the oracle
-only where the two screens order the shortlist boundary differently, which must be rare.  Where
+bf16 (fp8) screen ranks the candidate union of every query by the float64 distance to the
+bf16-rounded (E4M3-coded, row-scaled) points, keeps the R best and reranks them exactly; the GPU
+screen ranks the same union by |x~|^2 - 2 x~.q~ on the tensor cores, q~ the query's bf16 or E4M3
+parts, and is held to the rounding bound of that form (parity.screen_bounds).  As for the other
+screened kernels: every reported id must be a candidate reported with its float32 distance (1e-5
+relative), and a row may differ from the oracle only where the two screens order the shortlist
+boundary differently, which must be rare.  Where
 the shortlist holds every candidate the screen decides nothing, and the answer must equal the
 float32 search bit for bit.
 """
@@ -16,7 +18,7 @@ import torch
 import oracle
 import synth
 from oracle import screen
-from parity import assert_screened_close, assert_topk_close, candidate_sets
+from parity import assert_screened_close, assert_topk_close
 
 pytestmark = pytest.mark.gpu
 
@@ -58,37 +60,40 @@ def case(name):
 def gpu_forest(gf, X, F):
     G = gf.gf_forest_import(torch.from_numpy(X).cuda(), F.T, F.leaf_size, F.split_dim, F.split_val, F.perm)
     gf.gf_forest_add_screen(G, gf.GF_BF16_RERANK)
+    gf.gf_forest_add_screen(G, gf.GF_FP8_RERANK)
     return G
 
 
-def oracle_screen(F, X, Q, k, R):
+def oracle_screen(F, X, Q, k, R, prec="bf16"):
     offs, ids = oracle.candidates(F, oracle.descend(F, Q))
-    oi, od, _ = screen.screened_search(F, X, Q, k, R, "bf16", offs, ids)
-    return oi, od, candidate_sets(offs, ids)
+    oi, od, _ = screen.screened_search(F, X, Q, k, R, prec, offs, ids)
+    return oi, od, (offs, ids)
 
 
 @pytest.mark.parametrize("name", [c[0] for c in CASES])
 @pytest.mark.parametrize("R", [16, 32])
-def test_leaf_matches_oracle(gf, name, R):
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_leaf_matches_oracle(gf, name, R, prec):
     X, Q, F = case(name)
     G = gpu_forest(gf, X, F)
     k = 10
-    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.GF_BF16_RERANK, rerank_R=R,
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.PRECISIONS[prec], rerank_R=R,
                          algo=gf.GF_ALGO_LEAF)
-    oi, od, cands = oracle_screen(F, X, Q, k, R)
-    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+    oi, od, cands = oracle_screen(F, X, Q, k, R, prec)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, *cands, prec, R, "norm")
     assert gf.gf_kernel_status() == 0
 
 
 @pytest.mark.parametrize("k,R", [(1, 1), (1, 16), (5, 16), (7, 7)])
-def test_leaf_small_k(gf, k, R):
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_leaf_small_k(gf, k, R, prec):
     # shortlists shorter than a power of two and of length one
     X, Q, F = case("shared")
     G = gpu_forest(gf, X, F)
-    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.GF_BF16_RERANK, rerank_R=R,
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), k, precision=gf.PRECISIONS[prec], rerank_R=R,
                          algo=gf.GF_ALGO_LEAF)
-    oi, od, cands = oracle_screen(F, X, Q, k, R)
-    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+    oi, od, cands = oracle_screen(F, X, Q, k, R, prec)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, *cands, prec, R, "norm")
 
 
 @pytest.mark.parametrize("m", [1, 33])
@@ -97,10 +102,11 @@ def test_leaf_tiny_batches(gf, m):
     X, Q, F = case("tiny")
     G = gpu_forest(gf, X, F)
     Qs = np.ascontiguousarray(Q[:m])
-    gi, gd = gf.gf_query(G, torch.from_numpy(Qs).cuda(), 10, precision=gf.GF_BF16_RERANK, rerank_R=16,
-                         algo=gf.GF_ALGO_LEAF)
-    oi, od, cands = oracle_screen(F, X, Qs, 10, 16)
-    assert_screened_close(X, Qs, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+    for prec in ("bf16", "fp8"):
+        gi, gd = gf.gf_query(G, torch.from_numpy(Qs).cuda(), 10, precision=gf.PRECISIONS[prec], rerank_R=16,
+                             algo=gf.GF_ALGO_LEAF)
+        oi, od, cands = oracle_screen(F, X, Qs, 10, 16, prec)
+        assert_screened_close(X, Qs, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, *cands, prec, 16, "norm")
     fi, fd = gf.gf_query(G, torch.from_numpy(Qs).cuda(), 10, algo=gf.GF_ALGO_LEAF)
     oi, od = oracle.search(F, X, Qs, 10)
     assert_topk_close(X, Qs, fi.cpu().numpy(), fd.cpu().numpy(), oi, od)
@@ -115,19 +121,19 @@ def test_leaf_full_shortlist_equals_fp32(gf):
     assert G.info.cand_cap <= 32
     Qg = torch.from_numpy(Q).cuda()
     fi, fd = gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_STREAM)
-    li, ld = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF)
-    assert torch.equal(fi, li) and torch.equal(fd, ld)
+    for p in (gf.GF_BF16_RERANK, gf.GF_FP8_RERANK):
+        li, ld = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_LEAF)
+        assert torch.equal(fi, li) and torch.equal(fd, ld)
 
 
 def test_leaf_order_changes_no_result(gf):
     X, Q, F = case("shared")
     G = gpu_forest(gf, X, F)
     Qg = torch.from_numpy(Q).cuda()
-    a = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF,
-                    order=gf.GF_ORDER_GIVEN)
-    b = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF,
-                    order=gf.GF_ORDER_LOCALITY)
-    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    for p in (gf.GF_BF16_RERANK, gf.GF_FP8_RERANK):
+        a = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_LEAF, order=gf.GF_ORDER_GIVEN)
+        b = gf.gf_query(G, Qg, 10, precision=p, rerank_R=32, algo=gf.GF_ALGO_LEAF, order=gf.GF_ORDER_LOCALITY)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
 def test_leaf_caller_workspace_is_left_zero(gf):
@@ -151,7 +157,7 @@ def test_leaf_caller_workspace_is_left_zero(gf):
     assert torch.equal(s[0], t[0]) and torch.equal(s[1], t[1])
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_leaf_in_a_cuda_graph(gf, prec):
     # the benchmark's launch: captured once with a caller workspace (nothing allocates inside the
     # capture), replayed; the replays equal a direct call
@@ -207,7 +213,7 @@ def test_leaf_reflected_forest(gf):
     gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, precision=gf.GF_BF16_RERANK, rerank_R=32,
                          algo=gf.GF_ALGO_LEAF)
     oi, od, cands = oracle_screen(F, X, Q, 10, 32)
-    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, *cands, "bf16", 32, "norm")
 
 
 @pytest.mark.parametrize("c", [0, 24])
@@ -283,16 +289,17 @@ def test_leaf_priority_fp32_matches_oracle(gf, name, c):
 
 
 @pytest.mark.parametrize("name,c", PRIO_CASES)
-def test_leaf_priority_bf16_matches_oracle(gf, name, c):
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_leaf_priority_screened_matches_oracle(gf, name, c, prec):
     X, Q, F = case(name)
     G = gpu_forest(gf, X, F)
     R = 16
-    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, precision=gf.GF_BF16_RERANK, rerank_R=R,
+    gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, precision=gf.PRECISIONS[prec], rerank_R=R,
                          checks=c, algo=gf.GF_ALGO_LEAF)
     _, _, _, nl, seq = oracle.search_priority(F, X, Q, 10, c, return_leaves=True)
     offs, ids = priority_candidates(F, seq, nl)
-    oi, od, _ = screen.screened_search(F, X, Q, 10, R, "bf16", offs, ids)
-    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+    oi, od, _ = screen.screened_search(F, X, Q, 10, R, prec, offs, ids)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, offs, ids, prec, R, "norm")
 
 
 def test_leaf_priority_agrees_with_streaming(gf):
@@ -319,7 +326,7 @@ def test_leaf_at_its_limits(gf):
     assert_topk_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od)
     gi, gd = gf.gf_query(G, Qg, 10, precision=gf.GF_BF16_RERANK, rerank_R=32, algo=gf.GF_ALGO_LEAF)
     oi, od, cands = oracle_screen(F, X, Q, 10, 32)
-    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, cands)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, *cands, "bf16", 32, "norm")
 
     X, Q = synth.mixture(65_536, 8, 2000, "A", seed=7, qseed=8)
     F = oracle.build_forest(X, 64, 1, t=5, seed=13)
@@ -334,10 +341,9 @@ def test_leaf_at_its_limits(gf):
 def test_leaf_rejects_what_it_does_not_run(gf):
     X, Q, F = case("tiny")
     G = gpu_forest(gf, X, F)
-    gf.gf_forest_add_screen(G, gf.GF_FP8_RERANK)
     Qg = torch.from_numpy(Q).cuda()
-    for kw in (dict(precision=gf.GF_FP8_RERANK),                             # the fp8 screen
-               dict(precision=gf.GF_BF16_RERANK, rerank_R=33),               # shortlist above 32
+    for kw in (dict(precision=gf.GF_FP8_RERANK, rerank_R=33),                # shortlist above 32
+               dict(precision=gf.GF_BF16_RERANK, rerank_R=33),
                dict(precision=gf.GF_BF16_RERANK, rerank_R=16, checks=1024)):  # 1024 leaves x R > 8192
         with pytest.raises(gf.GFError) as e:
             gf.gf_query(G, Qg, 10, algo=gf.GF_ALGO_LEAF, **kw)

@@ -11,7 +11,7 @@ import torch
 import oracle
 import synth
 from oracle import screen
-from parity import RTOL, assert_screened_close, assert_topk_close, candidate_sets
+from parity import RTOL, assert_screened_close, assert_topk_close, candidate_sets, gpu_screen_scores
 
 pytestmark = pytest.mark.gpu
 
@@ -176,7 +176,8 @@ def test_query_screened(gf, prec, name):
     gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
     offs, ids = oracle.candidates(F, oracle.descend(F, Q))
     oi, od, _ = screen.screened_search(F, X, Q, k, R, prec, offs, ids)
-    assert_screened_close(X, Q, gi, gd, oi, od, candidate_sets(offs, ids))
+    assert_screened_close(X, Q, gi, gd, oi, od, offs, ids, prec, R, "direct",
+                          gpu_scores=gpu_screen_scores(gf, G, Q, offs, ids, prec))
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
@@ -294,7 +295,8 @@ def test_stream_large_screened(gf, prec, R):
     gi, gd = gf.gf_query(G, torch.from_numpy(Q).cuda(), 10, precision=gf.PRECISIONS[prec], rerank_R=R)
     offs, ids = oracle.candidates(F, oracle.descend(F, Q))
     oi, od, _ = screen.screened_search(F, X, Q, 10, R, prec, offs, ids)
-    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, candidate_sets(offs, ids))
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, offs, ids, prec, R, "direct",
+                          gpu_scores=gpu_screen_scores(gf, G, Q, offs, ids, prec))
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
