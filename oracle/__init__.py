@@ -68,6 +68,8 @@ def lib():
         L.gfo_search_reflected.argtypes = [P, i64, i32, P, P, P, i32, i32, P, i64, i32, P, P, P, P]
         L.gfo_search_reflected.restype = None
         L.gfo_search_priority.restype = None
+        L.gfo_search_f32.argtypes = [P, i64, i32, P, P, P, i32, i32, P, i64, i32, P, P]
+        L.gfo_search_f32.restype = None
         L.gfo_num_threads.argtypes = []; L.gfo_num_threads.restype = i32
         _lib = L
     return _lib
@@ -230,6 +232,21 @@ def search(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, return_ncand: bool =
                                _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
                                F.L, F.T, _p(Q), m, k, _Up(F), _p(oi), _p(od), _p(nc))
     return (oi, od, nc) if return_ncand else (oi, od)
+
+
+def search_f32(F: Forest, X: np.ndarray, Q: np.ndarray, k: int):
+    """The same search with float32 distance arithmetic in a plain loop (a CPU baseline to time,
+    not a reference): ids int64 [m, k], dists [m, k] (float32 values)."""
+    if F.U is not None:
+        raise ValueError("search_f32 takes plain forests only")
+    X, Q = _f32(X), _f32(Q)
+    m = Q.shape[0]
+    oi = np.empty((m, k), dtype=np.int64)
+    od = np.empty((m, k), dtype=np.float64)
+    lib().gfo_search_f32(_p(X), F.n, F.d, _p(np.ascontiguousarray(F.split_dim)),
+                         _p(np.ascontiguousarray(F.split_val)), _p(np.ascontiguousarray(F.perm)),
+                         F.L, F.T, _p(Q), m, k, _p(oi), _p(od))
+    return oi, od
 
 
 def search_priority(F: Forest, X: np.ndarray, Q: np.ndarray, k: int, c: int, eps: float = 0.0,

@@ -492,6 +492,49 @@ void gfo_search_reflected(const float *X, int64_t n, int32_t d, const int32_t *s
     }
 }
 
+/*
+ * The same search (Alg. 2 with c = T) with every distance in float32 arithmetic, a plain sequential
+ * loop: the CPU baseline of what a float32 search costs on the host, timed beside the float64
+ * search.  Not used as a reference for any result.  Its distances differ from gfo_dist2's by at
+ * most (d + 2) 2^-24 relative (a sum of d non-negative rounded terms, each rounded twice).
+ */
+static float dist2_f32(const float *q, const float *x, int32_t d) {
+    float s = 0.0f;
+    for (int32_t j = 0; j < d; j++) {
+        float e = q[j] - x[j];
+        s += e * e;
+    }
+    return s;
+}
+
+void gfo_search_f32(const float *X, int64_t n, int32_t d, const int32_t *split_dim,
+                    const float *split_val, const int32_t *perm, int32_t L, int32_t T, const float *Q,
+                    int64_t m, int32_t k, int64_t *out_ids, double *out_d) {
+    int64_t nn = ((int64_t)1 << L) - 1;
+    int64_t cap = ((n + ((int64_t)1 << L) - 1) >> L) * T;
+#pragma omp parallel
+    {
+        int32_t *leaf = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
+        int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+        res_t *r = (res_t *)malloc(sizeof(res_t) * (size_t)cap);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < m; i++) {
+            const float *q = Q + i * d;
+            for (int32_t t = 0; t < T; t++)
+                leaf[t] = (int32_t)gfo_descend_one(split_dim + t * nn, split_val + t * nn, L, q);
+            int64_t c = gfo_candidates_one(perm, n, L, T, leaf, cand);
+            for (int64_t j = 0; j < c; j++) {
+                r[j].id = cand[j];
+                r[j].dist = (double)dist2_f32(q, X + (int64_t)cand[j] * d, d);
+            }
+            take_k(r, c, k, out_ids + i * k, out_d + i * k);
+        }
+        free(leaf);
+        free(cand);
+        free(r);
+    }
+}
+
 /* ------------------------------------------------------------------ Alg. 2 priority search */
 
 /*

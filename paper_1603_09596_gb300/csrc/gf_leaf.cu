@@ -136,7 +136,9 @@ __device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, vola
     const uint64_t t0 = globaltimer();
     for (uint32_t spin = 1;; ++spin) {
         if (mbar_test(bar, parity)) return true;
-        if ((spin & 255) == 0) {
+        // the clock is read every 256 tries, or at every try under a limit shorter than the default
+        // (a test limit of a few hundred nanoseconds must be able to run out)
+        if ((spin & 255) == 0 || limit_ns < WAIT_NS) {
             if (*abort_flag) return false;
             if (globaltimer() - t0 > limit_ns) {
                 *abort_flag = 1;

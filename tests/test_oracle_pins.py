@@ -210,6 +210,26 @@ def test_leaf_size_at_least_n_is_exact_knn():
     np.testing.assert_allclose(d, rd, rtol=1e-12)
 
 
+def test_float32_search_is_the_float64_search_up_to_its_rounding():
+    # the float32 CPU baseline: same candidates, distances within (d + 2) 2^-24 of float64 (a sum of
+    # non-negative terms), ids equal except where two candidates lie within that bound
+    X, Q = synth.mixture(3000, 96, 60, "B", seed=9, qseed=10)
+    F = oracle.build_forest(X, 6, 24, seed=2)
+    oi, od = oracle.search(F, X, Q, 8)
+    fi, fd = oracle.search_f32(F, X, Q, 8)
+    tol = (X.shape[1] + 2) * 2.0 ** -24
+    fin = oi >= 0
+    assert np.array_equal(fi >= 0, fin)
+    assert np.all(np.abs(fd[fin] - od[fin]) <= tol * od[fin])
+    for i, j in zip(*np.nonzero((fi != oi) & fin)):
+        assert abs(oracle.dist2(Q[i], X[fi[i, j]]) - od[i, j]) <= 2 * tol * od[i, j]
+    # with one leaf holding everything it is a brute force in float32
+    F1 = oracle.build_forest(X[:500], 2, 500, seed=0)
+    bi, bd = oracle.search_f32(F1, X[:500], Q, 3)
+    ri, rd = _np_bruteforce(X[:500], Q, 3)
+    assert np.mean(bi == ri) >= 0.99
+
+
 def test_descent_follows_sign_of_eq1():
     X, Q = synth.mixture(1000, 16, 40, "A", seed=8)
     F = oracle.build_forest(X, 4, 30, seed=3)
