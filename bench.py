@@ -39,8 +39,9 @@ SPEC = dict(T=32, leaf_size=64)         # the tree parameters quoted with the wo
 
 
 # the query kernels' sources and the committed ncu traffic record of each headline algorithm
+# (the files that define the timed kernels; the C header's prose does not change them)
 _COMMON = ["paper_1603_09596_gb300/csrc/gf_internal.cuh", "paper_1603_09596_gb300/csrc/gf_device.cuh",
-           "paper_1603_09596_gb300/csrc/gf_score.cuh", "include/gf.h"]
+           "paper_1603_09596_gb300/csrc/gf_score.cuh"]
 KERNEL_SOURCES = {"stream": ["paper_1603_09596_gb300/csrc/gf_query.cu"] + _COMMON,
                   "leaf": ["paper_1603_09596_gb300/csrc/gf_leaf.cu"] + _COMMON}
 TRAFFIC_FILES = {"stream": os.path.join(ROOT, "profiles", "k_query_stream_traffic.json"),
@@ -143,31 +144,55 @@ def aggregate(ms_local: float, m_local: int, world: int, device=None):
     return world * m_local / (ms / 1e3), ms
 
 
-def exact_nn(torch, Xg, Qs, k):
-    """Exact k-NN of the sample Qs (evaluation only): float32 GEMM shortlist, float64 recheck."""
-    xn = (Xg * Xg).sum(1)
-    out_i, out_d = [], []
-    for s in range(0, Qs.shape[0], 128):
-        q = Qs[s:s + 128]
-        D = xn[None, :] - 2.0 * (q @ Xg.T)
-        cand = torch.topk(D, 64, dim=1, largest=False).indices
-        diff = Xg[cand].double() - q.double()[:, None, :]
-        ed = (diff * diff).sum(-1)
-        o = torch.argsort(ed, dim=1)[:, :k]
-        out_i.append(torch.gather(cand, 1, o))
-        out_d.append(torch.gather(ed, 1, o))
-    return torch.cat(out_i), torch.cat(out_d)
+def exact_cached(law, n, d, seed, qseed, m, nq, k):
+    """Exact neighbours of the first nq of the m queries from the committed cache the oracle's
+    brute force wrote (oracle/exact/, see oracle/exact_cache.py): (ids [nq, k], float64 squared
+    distances [nq, k]), or None.  Only the file is read here."""
+    p = os.path.join(ROOT, "oracle", "exact", f"law{law}_n{n}_d{d}_s{seed}_q{qseed}_m{m}_first{nq}_k{k}.json")
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    return np.array(j["ids"], dtype=np.int64), np.array(j["dist2"], dtype=np.float64)
 
 
-def recall(torch, Xg, Qs, ids, exact_i, exact_d):
-    ids = ids[:, :exact_i.shape[1]]
-    valid = ids[:, 0] >= 0
-    x0 = Xg[ids[:, 0].clamp(min=0)].double()
-    d0 = ((x0 - Qs.double()) ** 2).sum(1)
-    r1 = float(((d0 <= exact_d[:, 0]) & valid).double().mean())
-    k = exact_i.shape[1]
-    hits = (ids[:, :, None] == exact_i[:, None, :]).any(-1).double().sum(1) / k
-    return r1, float(hits.mean())
+def exact_scan(gf, Xg, Qs, k):
+    """Exact neighbours by the library's own float32 scan (a forest of one tree whose single leaf
+    holds every point), for workloads without an oracle cache: (ids, float64 distances)."""
+    from paper_1603_09596_gb300 import autotune
+    ids, _ = autotune.exact_neighbours(Xg, Qs, k)
+    ids = ids.cpu().numpy()
+    X = Xg.cpu().numpy()
+    Q = Qs.cpu().numpy().astype(np.float64)
+    d2 = ((X[ids].astype(np.float64) - Q[:, None, :]) ** 2).sum(-1)
+    return ids, d2
+
+
+def accuracy(X, Qs, ids, dists, exact):
+    """Recall and distance error of a result against the exact neighbours (Sec. 4: a query is a
+    miss unless its answer lies at the nearest distance; equal distances count as hits).
+      recall_at_1, recall_at_10: as usual (ids);
+      dist_rel_err_max / _median: |returned float32 distance - float64 distance of the returned id|
+        relative to the latter, over all returned results (the arithmetic's error);
+      approx_ratio_mean / _max: float64 distance of the i-th result over the i-th exact distance,
+        minus 1 (the search's approximation, the paper's epsilon, per result)."""
+    ids = np.asarray(ids)
+    dists = np.asarray(dists, dtype=np.float64)
+    ei, ed = exact
+    nq, k = ei.shape
+    ids, dists = ids[:nq, :k], dists[:nq, :k]
+    Q = np.asarray(Qs[:nq], dtype=np.float64)
+    valid = ids >= 0
+    d64 = ((X[np.where(valid, ids, 0)].astype(np.float64) - Q[:, None, :]) ** 2).sum(-1)
+    r1 = float(np.mean(valid[:, 0] & (d64[:, 0] <= ed[:, 0])))
+    r10 = float(np.mean([len(set(ids[i][valid[i]].tolist()) & set(ei[i].tolist())) / k for i in range(nq)]))
+    rel = np.abs(dists - d64)[valid] / np.maximum(d64[valid], 1e-30)
+    ratio = (d64 / np.maximum(ed, 1e-30) - 1.0)[valid]
+    return {"recall_at_1": r1, "recall_at_10": r10,
+            "dist_rel_err_max": float(rel.max()) if rel.size else None,
+            "dist_rel_err_median": float(np.median(rel)) if rel.size else None,
+            "approx_ratio_mean": float(ratio.mean()) if ratio.size else None,
+            "approx_ratio_max": float(ratio.max()) if ratio.size else None,
+            "sample": nq}
 
 
 def time_batch(gf, F, Qg, k, prec, steps, warmup, dev, world=1, local=0, no_graph=False, checks=0, algo=0, R=0):
@@ -229,29 +254,71 @@ def query_bytes(gf, F, prec, C, R, d, k, leaves=0):
     return rows + rerank + d * 4 + positions * 4 + 12 * k
 
 
-def leaf_bytes(gf, F, Qg, R, k, fp32=False):
-    """Algorithmic bytes of one leaf-major batch: every chunk (a (tree, leaf) bucket cut into groups
-    of at most 16 queries) reads its leaf's rows once -- bf16 with their ids and |x~|^2, or float32
-    with their ids; plus the query (read, split or padded), the (query, tree) lists written and
-    merged, the float32 rerank rows (bf16 screen) and the results.  The query rows re-read per row
-    tile come from L2 (a few tens of MB in all) and are not counted."""
+QP = {"fp32": 0, "bf16": 2, "fp8": 3}  # query parts of the tensor-core screens (MMA N = 16 QP)
+
+
+def leaf_stats(gf, F, Qg, R, k, prec):
+    """One leaf-major step, from the batch's own descent: chunks (a (tree, leaf) bucket cut into
+    groups of at most 16 queries), 128-row tiles, (row, query) pairs scored, MMAs issued, and the
+    algorithmic bytes -- every chunk reads its leaf's rows once (the screen's copy with its ids and
+    |x~|^2, and the E4M3 row scale), plus the queries (read, split), the (query, tree) lists written
+    and merged, the float32 rerank rows and the results.  The query parts re-read per row tile come
+    from L2 and are not counted."""
     import torch
     inf = F.info
-    m, T, L = Qg.shape[0], inf.T, inf.L
+    m, T, L, n, d = Qg.shape[0], inf.T, inf.L, inf.n, inf.d
     leaf = gf.gf_descend(F, Qg).long()
     u = (leaf + (torch.arange(T, device=Qg.device) << L)).flatten()
     cnt = torch.bincount(u, minlength=T << L)
     chunks = (cnt + 15) // 16
     b = torch.arange(T << L, device=Qg.device) & ((1 << L) - 1)
-    rows = ((b + 1) * inf.n >> L) - (b * inf.n >> L)
-    ldb, ldx = (inf.d + 7) // 8 * 8, (inf.d + 3) // 4 * 4
-    if fp32:
-        row_bytes = int((chunks * rows).sum()) * (ldx * 4 + 4)
-        other = m * inf.d * 4 + m * ldx * 4 * 2 + m * T * R * 8 * 2 + m * k * 12
+    rows = ((b + 1) * n >> L) - (b * n >> L)
+    tiles = int((chunks * ((rows + 127) // 128)).sum())
+    pairs = int((cnt * rows).sum())
+    ldx, ldb, ld8 = (d + 3) // 4 * 4, (d + 7) // 8 * 8, (d + 15) // 16 * 16
+    crow = int((chunks * rows).sum())
+    if prec == "fp32":
+        row_b, other = ldx * 4 + 4, m * d * 4 + m * ldx * 4 * 2 + m * T * k * 8 * 2 + m * k * 12
     else:
-        row_bytes = int((chunks * rows).sum()) * (ldb * 2 + 8)
-        other = m * inf.d * 4 * 2 + m * ldb * 2 * 2 + m * T * R * 8 * 2 + m * R * ldx * 4 + m * k * 12
-    return row_bytes + other, int(chunks.sum())
+        row_b = (ldb * 2 + 8) if prec == "bf16" else (ld8 + 12)
+        qb = ldb * 2 if prec == "bf16" else ld8
+        other = m * d * 4 * 2 + m * qb * QP[prec] + m * T * R * 8 * 2 + m * R * ldx * 4 + m * k * 12
+    esz = {"bf16": 2, "fp8": 1}.get(prec, 4)
+    mmas_per_tile = -(-d * esz // 32)  # one MMA per 32 bytes of the row (K = 16 bf16 or 32 E4M3)
+    return {"chunks": int(chunks.sum()), "tiles": tiles, "pairs": pairs, "bytes": crow * row_b + other,
+            "useful_flops": 2.0 * pairs * d * QP[prec],
+            "issued_flops": 2.0 * tiles * 128 * 16 * QP[prec] * mmas_per_tile * (32 // esz) if QP[prec] else 0.0}
+
+
+def time_kernel(gf, F, Qg, k, prec, algo, R, steps, dev, checks=0):
+    """Mean time per step of the path's scoring kernel alone (both launches on the leaf-major
+    path), from CUDA events the library records around its launches on the launching stream;
+    direct launches after a warm-up, one event pair per step."""
+    import torch
+    m = Qg.shape[0]
+    ids = torch.empty((m, k), dtype=torch.int64, device=dev)
+    dd = torch.empty((m, k), dtype=torch.float32, device=dev)
+    ws = torch.zeros(gf.gf_query_workspace_size(F, m, precision=prec, rerank_R=R, checks=checks, algo=algo) // 4 + 1,
+                     dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kw = dict(precision=prec, rerank_R=R, out=(ids, dd), workspace=ws, stream=s, checks=checks, algo=algo)
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            gf.gf_query(F, Qg, k, **kw)
+        for e in evs:
+            gf.gf_query(F, Qg, k, events=e, **kw)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def tensor_peaks():
+    """Dense bf16 TFLOP/s (burst, sustained) of the GB300s, and where the figure comes from."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["bf16_tflops"]), float(j.get("bf16_tflops_sustained", j["bf16_tflops"])), "measured"
+    return 1900.0, 1700.0, "fallback"
 
 
 def ours(args):
@@ -277,15 +344,23 @@ def ours(args):
     Qg = torch.from_numpy(Q).to(dev)
     stream = torch.cuda.current_stream(dev)
     hbm_peak, peak_kind = peaks()
+    bf16_peak, bf16_sust, tpeak_kind = tensor_peaks()
 
+    # the exact neighbours of the recall sample: the oracle's float64 brute force, cached per seed
     S = min(m, args.recall_sample)
-    ei, ed = exact_nn(torch, Xg, Qg[:S], k)
+    exact = exact_cached("B", n, d, 0, 1 + rank, m, S, k)
+    exact_src = "oracle float64 brute force (oracle/exact cache)"
+    if exact is None:
+        exact = exact_scan(gf, Xg, Qg[:S], k)
+        exact_src = "library float32 exact scan (no oracle cache for this workload)"
 
-    def time_query(F, prec, steps, warmup):
-        return time_batch(gf, F, Qg, k, prec, steps, warmup, dev, world, local, args.no_graph)
+    def evaluate(ids, dd):
+        return accuracy(X, Q, ids[:S].cpu().numpy(), dd[:S].cpu().numpy(), exact)
 
     def bytes_per_query(F, prec, C, R, leaves=0):
         return query_bytes(gf, F, prec, C, R, d, k, leaves)
+
+    algos = {gf.GF_ALGO_STREAM: "stream", gf.GF_ALGO_LEAF: "leaf"}
 
     def run_forest(T, p, tune_sample, checks=0, F=None):
         entry = {"T": T, "leaf_size": p}
@@ -296,6 +371,7 @@ def ours(args):
             torch.cuda.synchronize()
             entry["build_s"] = round(time.time() - tb, 3)
             gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
+            gf.gf_forest_add_screen(F, gf.GF_FP8_RERANK)
         entry["L"] = F.info.L
         if checks:
             entry["checks"] = checks
@@ -304,43 +380,44 @@ def ours(args):
         C = float(nc.double().mean())
         entry["cand_per_query"] = round(C, 1)
         leaves = gf.leaf_budget(F, checks) if checks else 0
-        runs = [("fp32_stream", gf.GF_FP32, gf.GF_ALGO_STREAM), ("bf16_stream", gf.GF_BF16_RERANK, gf.GF_ALGO_STREAM)]
+        runs = [("fp32_stream", "fp32", gf.GF_ALGO_STREAM), ("bf16_stream", "bf16", gf.GF_ALGO_STREAM)]
         if not checks:  # the leaf-major path runs the one-leaf-per-tree search
-            runs += [("fp32_leaf", gf.GF_FP32, gf.GF_ALGO_LEAF), ("bf16_leaf", gf.GF_BF16_RERANK, gf.GF_ALGO_LEAF)]
-        tuned = {}
-        for name, prec, algo in runs:
-            if prec not in tuned:
-                tuned[prec] = autotune.tune(F, Qg[:tune_sample], k, prec, checks=checks)
-            tr = tuned[prec]
+            runs += [("fp32_leaf", "fp32", gf.GF_ALGO_LEAF), ("bf16_leaf", "bf16", gf.GF_ALGO_LEAF),
+                     ("fp8_leaf", "fp8", gf.GF_ALGO_LEAF)]
+        for name, pn, algo in runs:
+            prec = gf.PRECISIONS[pn]
+            # kernel shape and shortlist: R is the shortest whose recall@1 and recall@10 on the tuning
+            # sample stay within 0.5 points of the float32 search's (the leaf-major path keeps at most 32)
+            tr = autotune.tune(F, Qg[:tune_sample], k, prec, checks=checks, X=Xg, algo=algo,
+                               r_max=32 if algo == gf.GF_ALGO_LEAF else 0)
             R = tr.get("R", 0)
-            if algo == gf.GF_ALGO_LEAF and R > 32:  # the leaf-major path keeps at most 32
-                continue
             ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, world, local,
                                          args.no_graph, checks, algo=algo, R=R)
-            r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
             mean_ms = statistics.mean(ms)
             if algo == gf.GF_ALGO_LEAF:
-                lb, nchunks = leaf_bytes(gf, F, Qg, R if prec != gf.GF_FP32 else k, k, prec == gf.GF_FP32)
-                bpq = lb / m
+                st = leaf_stats(gf, F, Qg, R if pn != "fp32" else k, k, pn)
+                bpq = st["bytes"] / m
             else:
-                bpq, nchunks = bytes_per_query(F, prec, C, R, leaves), None
-            entry[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4),
-                           "ms_min": round(min(ms), 4), "recall_at_1": r1, "recall_at_10": rk, "clocks": ck,
-                           "R": R, "algo": {gf.GF_ALGO_STREAM: "stream", gf.GF_ALGO_LEAF: "leaf"}[algo],
-                           "bytes_per_query": round(bpq),
-                           "achieved_gbs": round(bpq * m / (mean_ms / 1e3) / 1e9, 1)}
-            if algo == gf.GF_ALGO_LEAF:
-                entry[name]["chunks"] = nchunks
-            else:
-                entry[name].update(warps_per_cta=tr["warps"], ctas_per_sm=tr["ctas_per_sm"],
-                                   rows_in_flight=tr["rows_in_flight"])
-        for prec_name in ("fp32", "bf16"):
-            cands = [entry[nm] for nm in (prec_name + "_stream", prec_name + "_leaf") if nm in entry]
-            entry[prec_name] = max(cands, key=lambda e: e["qps"])
+                st, bpq = None, bytes_per_query(F, prec, C, R, leaves)
+            e = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4),
+                 "ms_min": round(min(ms), 4), "clocks": ck, "R": R, "algo": algos[algo],
+                 "bytes_per_query": round(bpq), "achieved_gbs": round(bpq * m / (mean_ms / 1e3) / 1e9, 1)}
+            e.update(evaluate(ids, dd))
+            if "recall" in tr:
+                e["tuning_recall"] = {str(r): v for r, v in tr["recall"].items()}
+            if st:
+                e["chunks"] = st["chunks"]
+            elif "warps" in tr:
+                e.update(warps_per_cta=tr["warps"], ctas_per_sm=tr["ctas_per_sm"], rows_in_flight=tr["rows_in_flight"])
+            entry[name] = e
+        for pn in ("fp32", "bf16", "fp8"):
+            cands = [entry[nm] for nm in (pn + "_stream", pn + "_leaf") if nm in entry]
+            if cands:
+                entry[pn] = max(cands, key=lambda e: e["qps"])
         return F, entry
 
     Fh, head = run_forest(HEADLINE["T"], HEADLINE["leaf_size"], args.tune_sample)
-    spec = prio = None
+    spec = prio = Fs = None
     if not args.skip_spec:
         Fs, spec = run_forest(SPEC["T"], SPEC["leaf_size"], args.tune_sample)
         if args.prio_checks > 0:
@@ -356,21 +433,59 @@ def ours(args):
     best = chosen["bf16"]
     Fc, cc = (Fh, 0) if point_id.startswith("one_leaf") else (Fs, args.prio_checks)
     value, mean_ms = aggregate(best["ms_per_step"], m, world, device=dev)
-    achieved = best["bytes_per_query"] * m / (mean_ms / 1e3) / 1e9
     algo = best["algo"]
+
+    # roofline of the dominant kernel, timed alone with CUDA events on its stream
+    gal = gf.GF_ALGO_LEAF if algo == "leaf" else gf.GF_ALGO_STREAM
+    kms = time_kernel(gf, Fc, Qg, k, gf.GF_BF16_RERANK, gal, best["R"], args.steps, dev, checks=cc)
     tr = recorded_traffic(algo)
     if tr and tr.get("point") != point_id:
         tr = None
-    kernel = ("k_leaf_score (2 launches: tree 0, then the rest; tcgen05 bf16 screen) dominant, with the "
-              "regrouping kernels and k_leaf_merge (dedupe + fp32 rerank + top-k); bytes and time of the whole step"
-              if algo == "leaf" else
-              "k_query_stream<bf16> (leaves + bitmap dedupe + bf16 screen + fp32 rerank + top-k), "
-              + ("k_prio_leaves + " if "priority" in point_id else "") + "1 query launch/step")
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": tr["bytes_per_launch"] if tr else None,
-            "traffic_note": tr["note"] if tr else "no ncu record for the current kernel sources",
-            "peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
-            "kernel": kernel, "bytes_per_query": best["bytes_per_query"]}
+    traffic = tr["bytes_per_launch"] if tr else None
+    alg_bytes = best["bytes_per_query"] * m
+    if algo == "leaf":
+        st = leaf_stats(gf, Fc, Qg, best["R"], k, "bf16")
+        kernel = ("k_leaf_score<bf16> (tcgen05 kind::f16 screen; 2 launches per step: the chunks of tree 0, then the "
+                  "rest), timed alone; bytes and flops of those launches")
+        per_query = bytes_per_query(Fc, gf.GF_BF16_RERANK, chosen["cand_per_query"], best["R"])
+        tensor = {"useful_tflops": round(st["useful_flops"] / (kms / 1e3) / 1e12, 2),
+                  "issued_tflops": round(st["issued_flops"] / (kms / 1e3) / 1e12, 2),
+                  "peak": bf16_peak, "unit": "TFLOP/s",
+                  "frac_useful": round(st["useful_flops"] / (kms / 1e3) / 1e12 / bf16_peak, 4),
+                  "frac_issued": round(st["issued_flops"] / (kms / 1e3) / 1e12 / bf16_peak, 4),
+                  "peak_kind": f"{tpeak_kind} cuBLAS bf16 burst (MEASURED_PEAKS bf16_tflops)",
+                  "note": "useful = (row, query) pairs x d x 2 flops x 2 query parts (hi, lo); issued adds the "
+                          "padding of chunks to 16 queries and of leaves to 128-row tiles"}
+    else:
+        st, tensor, per_query = None, None, None
+        kernel = ("k_query_stream<bf16> (leaves + bitmap dedupe + bf16 screen + fp32 rerank + top-k), "
+                  + ("k_prio_leaves + " if "priority" in point_id else "") + "1 query launch per step")
+    if traffic is not None:
+        dram_gbs = traffic / (kms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(dram_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(dram_gbs / hbm_peak, 4), "traffic": traffic,
+                "basis": "DRAM bytes of the kernel's launches in one step (ncu, committed record) / the kernel's "
+                         "live CUDA-event time"}
+    else:
+        alg_gbs = (st["bytes"] if st else alg_bytes) / (kms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(alg_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(alg_gbs / hbm_peak, 4), "traffic": None,
+                "basis": "algorithmic bytes / the kernel's live CUDA-event time (no ncu record for the current "
+                         "kernel sources)"}
+    roof.update({"peak_kind": f"{peak_kind} STREAM copy (MEASURED_PEAKS hbm_gbs)", "kernel": kernel,
+                 "kernel_ms": round(kms, 4), "step_ms": round(best["ms_per_step"], 4)})
+    if st:
+        roof["algorithmic"] = {"bytes": st["bytes"], "gbs": round(st["bytes"] / (kms / 1e3) / 1e9, 1),
+                               "frac": round(st["bytes"] / (kms / 1e3) / 1e9 / hbm_peak, 4),
+                               "note": "L2-assisted: each chunk's leaf rows counted once per chunk; most of them "
+                                       "come from L2 (the DRAM figure above is what HBM serves)"}
+        roof["per_query_model"] = {"bytes_per_query": round(per_query),
+                                   "gbs": round(per_query * m / (kms / 1e3) / 1e9, 1),
+                                   "note": "each query reading its own candidates' rows, as the streaming kernel "
+                                           "does; the leaf-major kernel shares every leaf read among the queries "
+                                           "that reach it"}
+        roof["tensor"] = tensor
+        roof["chunks"], roof["tiles"] = st["chunks"], st["tiles"]
 
     # end to end through the public API with host buffers.  Every step copies its queries from
     # pinned host memory and reads its ids and distances back; the copy of step j + 1's queries
@@ -395,7 +510,8 @@ def ours(args):
     def e2e_step(j):
         bi = j % 2
         stream.wait_event(h2d_done[bi])
-        gf.gf_query(Fc, Qd[bi], k, precision=gf.GF_BF16_RERANK, out=(ids, dd), checks=cc, stream=stream)
+        gf.gf_query(Fc, Qd[bi], k, precision=gf.GF_BF16_RERANK, rerank_R=best["R"], out=(ids, dd), checks=cc,
+                    stream=stream)
         q_done[bi].record(stream)
         with torch.cuda.stream(stream):
             ih.copy_(ids, non_blocking=True)
@@ -422,26 +538,31 @@ def ours(args):
            "d2h_bytes_per_step": m * k * 12}
 
     # latency under load: single-query requests to the headline forest with continuous batching
-    # (batches of at most 1024 through the streaming kernel, 4 slots).  The server's capacity is
-    # measured first (arrivals far above it for half a second); latency is then taken at Poisson
-    # arrivals of half that capacity.
+    # (batches of at most 1024, 4 slots).  The server's capacity is measured first (arrivals far
+    # above it for half a second); latency is then taken at Poisson arrivals of half that capacity.
     lat = None
     if not args.no_serve:
         srv = gf.Server([Fc], max_batch=1024, slots=4, hbm_budget_bytes=8 << 30, k_max=k,
                         precision=gf.GF_BF16_RERANK, rerank_R=best["R"], checks=cc)
         srv.run_poisson([Q[:4096]], rate_qps=5000, duration_s=0.3, k=k, seed=3)
-        cap = srv.run_poisson([Q], rate_qps=4.0 * chosen["bf16_stream"]["qps"], duration_s=0.5, k=k, seed=5)["qps"]
+        cap = srv.run_poisson([Q], rate_qps=4.0 * chosen["bf16"]["qps"], duration_s=0.5, k=k, seed=5)["qps"]
         rate = 0.5 * cap
-        st = srv.run_poisson([Q], rate_qps=rate, duration_s=args.serve_seconds, k=k, seed=4)
-        lat = {"capacity_qps": round(cap, 1), "offered_qps": round(rate, 1), "qps": round(st["qps"], 1),
-               "p50_ms": round(st["p50_ms"], 3),
-               "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 1),
-               "completed": st["completed"]}
+        st_srv = srv.run_poisson([Q], rate_qps=rate, duration_s=args.serve_seconds, k=k, seed=4)
+        lat = {"capacity_qps": round(cap, 1), "offered_qps": round(rate, 1), "qps": round(st_srv["qps"], 1),
+               "p50_ms": round(st_srv["p50_ms"], 3),
+               "p99_ms": round(st_srv["p99_ms"], 3), "mean_batch": round(st_srv["mean_batch"], 1),
+               "completed": st_srv["completed"]}
         srv.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(X, Q, Fc, gf, k, budget_s=args.cpu_budget, checks=cc)
+
+    configs = None
+    if not args.no_configs:
+        del Xg
+        torch.cuda.empty_cache()
+        configs = other_configs(args, gf, dev, X, Q, Fh)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -451,9 +572,12 @@ def ours(args):
                    "search": point_desc, "T": chosen["T"], "leaf_size": chosen["leaf_size"],
                    "checks": chosen.get("checks", chosen["T"]),
                    "precision": "bf16 screen + fp32 rerank", "R": best["R"],
-                   "recall_at_1": best["recall_at_1"], "recall_sample": S,
-                   "l2": "inputs larger than L2 (points 3.84 GB fp32 + 1.92 GB bf16)",
+                   "recall_at_1": best["recall_at_1"], "recall_sample": S, "exact_neighbours": exact_src,
+                   "l2": "inputs larger than L2 (points 3.84 GB fp32 + 1.92 GB bf16 + 0.96 GB e4m3)",
                    "parallelism": f"replicas x{world}"},
+        "accuracy": {key: best[key] for key in ("recall_at_1", "recall_at_10", "dist_rel_err_max",
+                                                "dist_rel_err_median", "approx_ratio_mean", "approx_ratio_max",
+                                                "sample")},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -464,14 +588,17 @@ def ours(args):
         "clocks": best["clocks"],
         "fp32_plain": chosen["fp32"],
         "bf16_screen": chosen["bf16"],
-        "paths": {name: {key: chosen[name][key] for key in ("qps", "algo", "R", "achieved_gbs", "recall_at_1")}
-                  for name in ("fp32_stream", "bf16_stream", "fp32_leaf", "bf16_leaf") if name in chosen},
+        "fp8_screen": chosen.get("fp8"),
+        "paths": {name: {key: chosen[name][key] for key in ("qps", "algo", "R", "achieved_gbs", "recall_at_1",
+                                                             "recall_at_10", "dist_rel_err_max")}
+                  for name in ("fp32_stream", "bf16_stream", "fp32_leaf", "bf16_leaf", "fp8_leaf") if name in chosen},
         "operating_points": {pid: {"bf16_qps": pt["bf16"]["qps"], "fp32_qps": pt["fp32"]["qps"],
                                    "recall_at_1": pt["bf16"]["recall_at_1"], "cand_per_query": pt["cand_per_query"]}
                              for pid, _, pt in points},
         "headline_forest": {kk: head[kk] for kk in ("T", "leaf_size", "L", "build_s", "cand_per_query")},
         "at_T32_p64": spec,
         "at_T32_p64_priority": prio,
+        "configs": configs,
         "gen_s": round(gen_s, 2),
         "serving": lat,
         "p99_ms": lat["p99_ms"] if lat else None,
@@ -483,24 +610,137 @@ def ours(args):
 
 
 def cpu_baseline(X, Q, F, gf, k, budget_s=15.0, checks=0):
-    """The oracle search, as it stands, on this host's cores over a bounded query sample."""
+    """The oracle search, as it stands, on this host's cores over a bounded query sample, and beside
+    it the same search with float32 distances in a plain loop (a fairer CPU figure)."""
     import oracle
     sd, sv, pm = gf.gf_forest_export(F)
     inf = F.info
     Fo = oracle.Forest(inf.n, inf.d, inf.T, inf.leaf_size, inf.L, sd, sv, pm)
-    done, t0, bs = 0, time.time(), 64
-    while time.time() - t0 < budget_s and done < Q.shape[0]:
-        if checks:
-            oracle.search_priority(Fo, X, Q[done:done + bs], k, checks)
-        else:
-            oracle.search(Fo, X, Q[done:done + bs], k)
-        done += min(bs, Q.shape[0] - done)
-        bs = min(bs * 2, 1024)
-    el = time.time() - t0
+
+    def timed(fn, budget):
+        done, t0, bs = 0, time.time(), 64
+        while time.time() - t0 < budget and done < Q.shape[0]:
+            fn(Q[done:done + bs])
+            done += min(bs, Q.shape[0] - done)
+            bs = min(bs * 2, 1024)
+        return done, time.time() - t0
+
+    if checks:
+        done, el = timed(lambda q: oracle.search_priority(Fo, X, q, k, checks), budget_s)
+    else:
+        done, el = timed(lambda q: oracle.search(Fo, X, q, k), budget_s)
     search = f"priority search, c={checks}" if checks else "one leaf per tree"
-    return {"value": round(done / el, 2), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{done} of the {Q.shape[0]} queries, same forest (T={inf.T}, leaf_size={inf.leaf_size}), "
-                      f"{search}, float64"}
+    out = {"value": round(done / el, 2), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{done} of the {Q.shape[0]} queries, same forest (T={inf.T}, leaf_size={inf.leaf_size}), "
+                     f"{search}, float64"}
+    if not checks:
+        d32, e32 = timed(lambda q: oracle.search_f32(Fo, X, q, k), budget_s / 2)
+        out["fp32_loop"] = {"value": round(d32 / e32, 2), "unit": UNIT, "cores": oracle.num_threads(),
+                            "kind": "float32 plain loop (oracle/gf_oracle.c gfo_search_f32)",
+                            "sample": f"{d32} of the {Q.shape[0]} queries, same forest, one leaf per tree"}
+    return out
+
+
+def run_config(gf, dev, args, name, law, n, d, m, T, p, ks=(10,), precs=("fp32", "bf16"), sample=1000,
+               shapes=None):
+    """One workload: build its forest, time every precision's search (CUDA graph, AUTO kernel), and
+    measure recall and distance error against the oracle's cached exact neighbours."""
+    import torch
+    import synth
+    from paper_1603_09596_gb300 import autotune
+    t0 = time.time()
+    X, Q = synth.mixture(n, d, m, law, seed=0, qseed=1)
+    gen_s = time.time() - t0
+    Xg, Qg = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    torch.cuda.synchronize()
+    tb = time.time()
+    F = gf.gf_build(Xg, T, p, t=min(5, d), seed=0)
+    torch.cuda.synchronize()
+    out = {"workload": f"law-{law} Gaussian mixture n={n} d={d}, m={m} queries", "T": T, "leaf_size": p,
+           "L": F.info.L, "build_s": round(time.time() - tb, 3), "gen_s": round(gen_s, 1)}
+    for pn in precs:
+        if pn != "fp32":
+            gf.gf_forest_add_screen(F, gf.PRECISIONS[pn])
+    for k in ks:
+        nq = min(sample, m)
+        exact = exact_cached(law, n, d, 0, 1, m, nq, 10)
+        src = "oracle float64 brute force (cached)"
+        if exact is None:
+            exact = exact_scan(gf, Xg, Qg[:nq], 10)
+            src = "library float32 exact scan"
+        exact = (exact[0][:, :k], exact[1][:, :k])
+        for pn in precs:
+            prec = gf.PRECISIONS[pn]
+            tr = autotune.tune(F, Qg[:min(m, 500 if d > 2000 else 2000)], k, prec, X=Xg,
+                               **({"shapes": shapes} if shapes else {}))
+            R = tr.get("R", 0)
+            ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, R=R)
+            mean_ms = statistics.mean(ms)
+            e = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4), "R": R,
+                 "exact_neighbours": src}
+            if "recall" in tr:
+                e["tuning_recall"] = {str(r): v for r, v in tr["recall"].items()}
+            e.update(accuracy(X, Q, ids[:nq].cpu().numpy(), dd[:nq].cpu().numpy(), exact))
+            out[f"{pn}_k{k}"] = e
+    F.free()
+    del Xg, Qg
+    torch.cuda.empty_cache()
+    return out
+
+
+def serve_config(gf, dev, args, Xh, Qh, Fh):
+    """Six resident forests of uneven size under Poisson arrivals at 5k-200k queries/s (targets
+    uniform over the forests), k = 10: throughput and p50/p99 latency per rate.  The 10^6 x 960
+    forest is the headline's."""
+    import torch
+    import synth
+    forests, queries = [], []
+    t0 = time.time()
+    for i, (n, d, T, p) in enumerate(SERVE_FORESTS):
+        if (n, d) == (Xh.shape[0], Xh.shape[1]) and Fh is not None:
+            forests.append(Fh)
+            queries.append(Qh[:2048])
+            continue
+        X, Q = synth.mixture(n, d, 2048, "B", seed=100 + i, qseed=200 + i)
+        F = gf.gf_build(torch.from_numpy(X).to(dev), T, p, seed=i)
+        gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
+        forests.append(F)
+        queries.append(Q)
+    setup_s = time.time() - t0
+    S = gf.Server(forests, max_batch=1024, slots=args.serve_slots, hbm_budget_bytes=args.serve_budget << 30,
+                  k_max=10, precision=gf.GF_BF16_RERANK, rerank_R=32)
+    S.run_poisson(queries, rate_qps=5000, duration_s=0.3, k=10, seed=1)  # warm-up
+    rates = []
+    for rate in SERVE_RATES:
+        st = S.run_poisson(queries, rate_qps=rate, duration_s=args.serve_seconds, k=10, seed=rate)
+        rates.append({"offered_qps": rate, "qps": round(st["qps"], 1), "p50_ms": round(st["p50_ms"], 3),
+                      "p99_ms": round(st["p99_ms"], 3), "max_ms": round(st["max_ms"], 3),
+                      "mean_batch": round(st["mean_batch"], 1), "completed": st["completed"]})
+    out = {"forests": [dict(n=n, d=d, T=T, leaf_size=p) for n, d, T, p in SERVE_FORESTS], "slots": S.slots,
+           "precision": "bf16 screen + fp32 rerank, R=32", "setup_s": round(setup_s, 1), "rates": rates}
+    S.close()
+    for F in forests:
+        if F is not Fh:
+            F.free()
+    return out
+
+
+def other_configs(args, gf, dev, Xh, Qh, Fh):
+    """The workloads beside the headline: tiny 10^4 x 128 (k = 1 and 10), batched 10^5 x 960,
+    high-d 2 x 10^5 x 10^4 (float32 / bf16 / E4M3 screens) and the six-forest serving load."""
+    out = {}
+    t0 = time.time()
+    out["tiny_1e4x128"] = run_config(gf, dev, args, "tiny", "A", 10_000, 128, 100, 8, 32, ks=(1, 10),
+                                     precs=("fp32",), sample=100)
+    out["batched_1e5x960"] = run_config(gf, dev, args, "batched", "B", 100_000, 960, 10_000, 16, 64,
+                                        precs=("fp32", "bf16"))
+    out["highd_2e5x1e4"] = run_config(gf, dev, args, "highd", "C", 200_000, 10_000, 2_000, 24, 32,
+                                      precs=("fp32", "bf16", "fp8"), sample=200,
+                                      shapes=[(8, 0, 0), (4, 0, 0), (8, 2, 0), (4, 2, 0)])
+    if not args.no_serve:
+        out["serving_6_forests"] = serve_config(gf, dev, args, Xh, Qh, Fh)
+    out["seconds"] = round(time.time() - t0, 1)
+    return out
 
 
 def profile(args):
@@ -533,43 +773,13 @@ def profile(args):
 
 
 def highd(args):
-    """The d = 10^4 workload: float32 vs bf16 vs FP8-E4M3 screening (+ float32 rerank)."""
+    """The d = 10^4 workload alone: float32 vs bf16 vs FP8-E4M3 screening (+ float32 rerank)."""
     import torch
     import paper_1603_09596_gb300 as gf
-    from paper_1603_09596_gb300 import autotune
-    import synth
-    n, d, m, T, p, k = 200_000, 10_000, 2_000, 24, 32, 10
-    X, Q = synth.mixture(n, d, m, "C", seed=0, qseed=1)
-    dev = torch.device("cuda", 0)
-    Xg, Qg = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
-    del X
-    S = min(m, args.recall_sample)
-    ei, ed = exact_nn(torch, Xg, Qg[:S], k)
-    tb = time.time()
-    F = gf.gf_build(Xg, T, p, seed=0)
-    torch.cuda.synchronize()
-    build_s = time.time() - tb
-    gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
-    gf.gf_forest_add_screen(F, gf.GF_FP8_RERANK)
-    nc = torch.empty((m,), dtype=torch.int32, device=dev)
-    gf.gf_query(F, Qg, k, algo=gf.GF_ALGO_STREAM, ncand_out=nc)
-    C = float(nc.double().mean())
-    hbm_peak, _ = peaks()
-    out = {}
-    for name in ("fp32", "bf16", "fp8"):
-        prec = gf.PRECISIONS[name]
-        tr = autotune.tune(F, Qg[:min(m, 1000)], k, prec)
-        ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, no_graph=args.no_graph)
-        r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
-        mean_ms = statistics.mean(ms)
-        bpq = query_bytes(gf, F, prec, C, tr.get("R", 0), d, k)
-        out[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4),
-                     "recall_at_1": r1, "recall_at_10": rk, "R": tr.get("R", 0),
-                     "achieved_gbs": round(bpq * m / (mean_ms / 1e3) / 1e9, 1),
-                     "frac_of_hbm": round(bpq * m / (mean_ms / 1e3) / 1e9 / hbm_peak, 4), "clocks": ck}
+    out = run_config(gf, torch.device("cuda", 0), args, "highd", "C", 200_000, 10_000, 2_000, 24, 32,
+                     precs=("fp32", "bf16", "fp8"), sample=200)
     print(json.dumps({"metric": "queries/s at 2e5 x 1e4, k=10: fp8 / bf16 screen + fp32 rerank vs fp32",
-                      "unit": "queries/s", "n": n, "d": d, "m": m, "T": T, "leaf_size": p,
-                      "cand_per_query": round(C, 1), "build_s": round(build_s, 2), "results": out}))
+                      "unit": "queries/s", **out}))
 
 
 def klein(args):
@@ -584,7 +794,7 @@ def klein(args):
     dev = torch.device("cuda", 0)
     Xg, Qg = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
     S = min(m, args.recall_sample)
-    ei, ed = exact_nn(torch, Xg, Qg[:S], k)
+    exact = exact_scan(gf, Xg, Qg[:S], k)
     tb = time.time()
     F = gf.gf_build(Xg, T, p, seed=0)
     torch.cuda.synchronize()
@@ -595,14 +805,15 @@ def klein(args):
         prec = gf.PRECISIONS[name]
         tr = autotune.tune(F, Qg[:min(m, 2000)], k, prec)
         ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, no_graph=args.no_graph)
-        r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
-        got = Xg[ids[:S, 0].clamp(min=0)].double()
-        dr = ((got - Qg[:S].double()) ** 2).sum(1).sqrt()
-        de = ed[:, 0].sqrt()
-        eps_miss = {str(e): float(((dr > (1 + e) * de) | (ids[:S, 0] < 0)).double().mean()) for e in (0.0, 0.1, 0.5, 0.9)}
+        acc = accuracy(X, Q, ids[:S].cpu().numpy(), dd[:S].cpu().numpy(), exact)
+        # the epsilon-miss rate of Sec. 4: the first answer farther than (1 + eps) times the nearest
+        idn = ids[:S, 0].cpu().numpy()
+        dr = np.sqrt(((X[np.maximum(idn, 0)].astype(np.float64) - Q[:S].astype(np.float64)) ** 2).sum(1))
+        de = np.sqrt(exact[1][:, 0])
+        eps_miss = {str(e): float(np.mean((dr > (1 + e) * de) | (idn < 0))) for e in (0.0, 0.1, 0.5, 0.9)}
         mean_ms = statistics.mean(ms)
-        out[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4), "recall_at_1": r1,
-                     "recall_at_10": rk, "eps_miss": eps_miss, "R": tr.get("R", 0), "clocks": ck}
+        out[name] = {"qps": round(m / (mean_ms / 1e3), 1), "ms_per_step": round(mean_ms, 4), **acc,
+                     "eps_miss": eps_miss, "R": tr.get("R", 0), "clocks": ck}
     print(json.dumps({"metric": "queries/s, noisy Klein bottle in R^100, n=10^6, k=10", "unit": "queries/s",
                       "n": n, "d": d, "m": m, "T": T, "leaf_size": p, "build_s": round(build_s, 2),
                       "results": out}))
@@ -623,7 +834,7 @@ def householder(args):
     U = rng.standard_normal((T, d))
     U = (U / np.linalg.norm(U, axis=1, keepdims=True)).astype(np.float32)
     S = min(m, args.recall_sample)
-    ei, ed = exact_nn(torch, Xg, Qg[:S], k)
+    exact = exact_cached("B", n, d, 0, 1, m, S, k) or exact_scan(gf, Xg, Qg[:S], k)
     out = {}
     for name, UU in (("plain", None), ("reflected", U)):
         torch.cuda.synchronize()
@@ -637,9 +848,8 @@ def householder(args):
             prec = gf.PRECISIONS[pn]
             tr = autotune.tune(F, Qg[:min(m, 2000)], k, prec)
             ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, no_graph=args.no_graph)
-            r1, rk = recall(torch, Xg, Qg[:S], ids[:S], ei, ed)
-            res[pn] = {"qps": round(m / (statistics.mean(ms) / 1e3), 1), "recall_at_1": r1, "recall_at_10": rk,
-                       "R": tr.get("R", 0)}
+            acc = accuracy(X, Q, ids[:S].cpu().numpy(), dd[:S].cpu().numpy(), exact)
+            res[pn] = {"qps": round(m / (statistics.mean(ms) / 1e3), 1), **acc, "R": tr.get("R", 0)}
         out[name] = res
         F.free()
     print(json.dumps({"metric": "Householder reflection per tree (Sec. 2.2) vs none, headline workload",
@@ -738,6 +948,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--skip-spec", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the workloads beside the headline")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--prio-checks", type=int, default=512, help="leaf checks c of the priority-search point")
     ap.add_argument("--tune-sample", type=int, default=2000)

@@ -341,8 +341,11 @@ int gf_score_screened(const gf_forest *F, const float *Q, int64_t m, const int32
  * HBM admission rule -- a batch is dispatched exactly when a slot and its memory are free.  A
  * dispatcher thread takes up to max_batch requests of the forest whose oldest request waited
  * longest; batches on different slots overlap on the device; requests arriving meanwhile join the
- * next batch.  Every request's answer equals gf_query on that query alone (same kernel, same
- * arithmetic).  The forests must outlive the server and must not be freed while it runs.
+ * next batch.  A batch runs the streaming kernel, whose answers equal gf_query on each query
+ * alone (same kernel, same arithmetic), or -- when the server allows it and the batch is large
+ * enough to share leaves -- the leaf-major path, whose answers are those of the same search within
+ * the screens' tolerance (a screened score is computed in another form there).  The forests must
+ * outlive the server and must not be freed while it runs.
  */
 typedef struct gf_server gf_server;
 
@@ -355,6 +358,9 @@ typedef struct gf_server_opts {
     int32_t rerank_R;          /* shortlist for the screened precisions (0 = forest default) */
     int32_t checks;            /* leaf checks c of every batch (gf_query_opts.checks) */
     double eps;                /* gf_query_opts.eps */
+    int32_t algo;              /* GF_ALGO_AUTO (default): a batch that shares leaves enough (the rule
+                                  of GF_ALGO_AUTO) runs the leaf-major path, any other the streaming
+                                  kernel; GF_ALGO_STREAM: the streaming kernel always */
 } gf_server_opts;
 
 typedef struct gf_server_stats {

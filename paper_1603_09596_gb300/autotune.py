@@ -3,9 +3,12 @@
 For a resident forest and a sample of queries it
   1. times every (warps per CTA, CTAs per SM) shape of the query kernel in each precision and
      keeps the fastest;
-  2. for a screened precision, picks the shortest shortlist R whose answers agree with the
-     float32 search on at least `agree` of the sample's top-k entries (the screen only decides
-     which candidates get the exact float32 rerank, so this is what R trades away);
+  2. for a screened precision, picks the shortest shortlist R that costs the search no accuracy
+     (the screen only decides which candidates get the exact float32 rerank, so this is what R
+     trades away): given the points X, the shortest R whose recall@1 and recall@10 on the sample,
+     against the exact neighbours (the library's own exact scan), are within `tol` of the float32
+     search's; without X, the shortest R whose answers agree with the float32 search on at least
+     `agree` of the sample's top-k entries;
 and stores the choice in the forest (gf_forest_set_tuning), where gf_query picks it up.
 Results are cached per (n, d, T, leaf_size, k, precision, batch) for the process.
 """
@@ -19,7 +22,7 @@ _cache: dict = {}
 
 # (warps per CTA, CTAs per SM (0 = occupancy), rows in flight per warp (0 = default))
 SHAPES = [(w, c, g) for w in (4, 8) for c in (0, 2, 3) for g in (0, 2, 4)] + [(16, 0, 0), (16, 1, 0)]
-R_CHOICES = [16, 32, 64, 128, 256]
+R_CHOICES = [16, 24, 32, 48, 64, 128, 256]
 
 
 def _time(fn, reps: int = 3) -> float:
@@ -36,10 +39,19 @@ def _time(fn, reps: int = 3) -> float:
     return best
 
 
+def _recalls(ids: torch.Tensor, dists: torch.Tensor, ex_ids: torch.Tensor, ex_d: torch.Tensor):
+    """recall@1 (the first answer at the exact nearest distance; equal distances count, Sec. 4) and
+    recall@k of a result against exact neighbours."""
+    r1 = float(((dists[:, 0] <= ex_d[:, 0]) & (ids[:, 0] >= 0)).float().mean())
+    rk = float((ids[:, :, None] == ex_ids[:, None, :]).any(-1).float().mean())
+    return r1, rk
+
+
 def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0.995,
-         shapes=SHAPES, r_choices=R_CHOICES, checks: int = 0) -> dict:
+         shapes=SHAPES, r_choices=R_CHOICES, checks: int = 0, X: torch.Tensor | None = None,
+         tol: float = 0.005, algo: int = gf.GF_ALGO_AUTO, r_max: int = 0) -> dict:
     inf = F.info
-    key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0], checks)
+    key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0], checks, X is not None, algo, r_max)
     if key in _cache:
         res = _cache[key]
         gf.gf_forest_set_tuning(F, precision, res["warps"], res["ctas_per_sm"], res.get("R", 0),
@@ -48,23 +60,40 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
     res: dict = {"precision": precision}
     R = 0
     if precision != gf.GF_FP32:
-        ref_ids, _ = gf.gf_query(F, Q, k, checks=checks)
-        R = r_choices[-1]
-        for r in r_choices:
-            if r < k:
-                continue
-            ids, _ = gf.gf_query(F, Q, k, precision=precision, rerank_R=r, checks=checks)
-            hit = (ids[:, :, None] == ref_ids[:, None, :]).any(-1).float().mean().item()
-            res.setdefault("agreement", {})[r] = hit
-            if hit >= agree:
-                R = r
-                break
+        choices = [r for r in r_choices if r >= k and (r_max <= 0 or r <= r_max)]
+        if r_max > 0 and r_max not in choices and r_max >= k:
+            choices.append(r_max)
+        R = choices[-1]
+        ref_ids, ref_d = gf.gf_query(F, Q, k, checks=checks)
+        if X is not None:
+            # accuracy parity with the float32 search against the exact neighbours
+            ex_ids, ex_d = _exact(X, Q, k)
+            ref = _recalls(ref_ids, ref_d, ex_ids, ex_d)
+            res["criterion"] = f"recall@1 and recall@{k} within {tol} of float32's {ref}"
+            for r in choices:
+                ids, d = gf.gf_query(F, Q, k, precision=precision, rerank_R=r, checks=checks, algo=algo)
+                got = _recalls(ids, d, ex_ids, ex_d)
+                res.setdefault("recall", {})[r] = got
+                if got[0] >= ref[0] - tol and got[1] >= ref[1] - tol:
+                    R = r
+                    break
+        else:
+            res["criterion"] = f"top-{k} ids agree with float32's on {agree} of entries"
+            for r in choices:
+                ids, _ = gf.gf_query(F, Q, k, precision=precision, rerank_R=r, checks=checks, algo=algo)
+                hit = (ids[:, :, None] == ref_ids[:, None, :]).any(-1).float().mean().item()
+                res.setdefault("agreement", {})[r] = hit
+                if hit >= agree:
+                    R = r
+                    break
         res["R"] = R
     timings = {}
+    if algo == gf.GF_ALGO_LEAF:
+        shapes = [(inf_w, 0, 0) for inf_w in (8,)]  # the leaf-major kernels have one shape
     for w, c, g in shapes:
         try:
             t = _time(lambda: gf.gf_query(F, Q, k, precision=precision, rerank_R=R, warps_per_cta=w,
-                                          ctas_per_sm=c, rows_in_flight=g, checks=checks))
+                                          ctas_per_sm=c, rows_in_flight=g, checks=checks, algo=algo))
         except gf.GFError:
             continue
         timings[(w, c, g)] = t
@@ -87,6 +116,17 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
 # configuration whose recall@1 reaches the target.
 
 DEFAULT_GRID = [(T, p, c) for T in (16, 32) for p in (64, 256, 1024) for c in (0,)]
+
+
+_exact_cache: dict = {}
+
+
+def _exact(X: torch.Tensor, Q: torch.Tensor, k: int):
+    key = (X.data_ptr(), tuple(X.shape), Q.data_ptr(), tuple(Q.shape), k)
+    if key not in _exact_cache:
+        _exact_cache.clear()
+        _exact_cache[key] = exact_neighbours(X, Q, k)
+    return _exact_cache[key]
 
 
 def exact_neighbours(X: torch.Tensor, Q: torch.Tensor, k: int = 1):

@@ -73,8 +73,10 @@ template <int FMT>
 struct LeafCfg {
     static constexpr int QP = FMT == LF_FP8 ? 3 : 2;       // query parts
     static constexpr int ESZ = FMT == LF_FP8 ? 1 : 2;      // bytes per value
-    static constexpr int SUB = 3;        // sub-tiles (128-byte k-slices) per stage: one wait, one release
-    static constexpr int STAGES = 3;     // shared-memory pipeline depth
+    // sub-tiles (128-byte k-slices) per stage -- one wait and one release each -- and stages: for
+    // E4M3, four stages of two, a ring of eight k-slices, which a 960-value row fills exactly
+    static constexpr int SUB = FMT == LF_FP8 ? 2 : 3;
+    static constexpr int STAGES = FMT == LF_FP8 ? 4 : 3;
     static constexpr int PROD_WARPS = SUB * STAGES;  // producer warps; each loads whole sub-tiles
     static constexpr int A_BYTES = BM * 128;
     static constexpr int B_BYTES = NQ * 128;         // one query part of the chunk
@@ -293,11 +295,11 @@ __device__ __forceinline__ unsigned long long warp_merge_top(unsigned long long 
 }
 
 // Add the keys of the lanes in `bl` (all below the list's R-th key when the ballot was taken) to
-// the list: one by one when they are few, else sorted and merged.
+// the list: one by one when they are few (eight or fewer), else sorted and merged.
 __device__ __noinline__ unsigned long long list_add(unsigned long long lst, unsigned long long key, unsigned bl, int R,
                                                     int RL) {
     const int lane = threadIdx.x & 31;
-    if (__popc(bl) > 4) return warp_merge_top(lst, warp_sort32((bl >> lane) & 1u ? key : KEY_NONE), RL);
+    if (__popc(bl) > 8) return warp_merge_top(lst, warp_sort32((bl >> lane) & 1u ? key : KEY_NONE), RL);
     while (bl) {
         const int src = __ffs(bl) - 1;
         bl &= bl - 1;
@@ -400,10 +402,15 @@ __global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestV
         // h % PROD_WARPS.  The warp copies the whole sub-tile (lane: one 16-byte column chunk of
         // every fourth row), waits for its own copies, makes them visible to the tensor cores and
         // arrives on the stage's full barrier: no sub-tile waits for another one's copies.
+        // A warp always fills the same ring slot (PROD_WARPS sub-tiles make one turn of the ring), so
+        // the query parts it copied last are still there: when a row tile takes exactly one turn of
+        // the ring, every later tile of the chunk finds its k-slice's parts in place and the warp
+        // copies the leaf rows alone.
         const int pw = warp - 4;
         const int c = lane & 7, r0 = lane >> 3;  // column chunk; rows r0, r0 + 4, ...
         uint32_t it = 0;                          // stages of the CTA's earlier chunks
         bool ok = true;
+        int held_w = -1, held_k = -1;             // chunk and k-slice of the query parts in the slot
         for (int w = item_lo + blockIdx.x; w < item_hi && ok; w += gridDim.x) {
             int t, rows, q0pos, nq;
             long long lo;
@@ -446,15 +453,19 @@ __global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestV
                     const unsigned char *src = live ? xrows + (size_t)ids[i] * pitch + col : xrows;
                     cp_async16(sa + r * 128 + ((c ^ (r & 7)) << 4), src, live ? nb : 0);
                 }
+                if (held_w != w || held_k != kbyte) {
+                    held_w = w;
+                    held_k = kbyte;
 #pragma unroll
-                for (int h = 0; h < QP; ++h) {
-                    const unsigned char *qb = A.qpart + h * A.qpart_stride;
+                    for (int h = 0; h < QP; ++h) {
+                        const unsigned char *qb = A.qpart + h * A.qpart_stride;
 #pragma unroll
-                    for (int i = 0; i < NQ / 4; ++i) {
-                        const int j = r0 + 4 * i;
-                        const bool live = qid[i] >= 0 && nb > 0;
-                        const unsigned char *src = live ? qb + (size_t)qid[i] * pitch + col : qb;
-                        cp_async16(sa + A_BYTES + h * B_BYTES + j * 128 + ((c ^ (j & 7)) << 4), src, live ? nb : 0);
+                        for (int i = 0; i < NQ / 4; ++i) {
+                            const int j = r0 + 4 * i;
+                            const bool live = qid[i] >= 0 && nb > 0;
+                            const unsigned char *src = live ? qb + (size_t)qid[i] * pitch + col : qb;
+                            cp_async16(sa + A_BYTES + h * B_BYTES + j * 128 + ((c ^ (j & 7)) << 4), src, live ? nb : 0);
+                        }
                     }
                 }
                 cp_async_commit();

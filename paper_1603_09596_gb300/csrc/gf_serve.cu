@@ -98,6 +98,17 @@ static void release_slot_memory(Slot &s) {
     s = Slot();
 }
 
+// The kernel of a batch of m queries on F: the leaf-major path when the server allows it and the
+// batch shares leaves enough for it to pay (the rule of GF_ALGO_AUTO), else the streaming kernel.
+static int32_t batch_algo(const gf_server *S, const gf_forest *F, int64_t m, int32_t k) {
+    if (S->opts.algo == GF_ALGO_STREAM) return GF_ALGO_STREAM;
+    const int p = S->opts.precision;
+    const int R = S->opts.rerank_R > 0 ? S->opts.rerank_R : F->tune_R[p];
+    QueryExtra x;
+    x.leaf_budget = leaf_budget_of(F, S->opts.checks, S->opts.eps);
+    return gf_leaf_preferred(F, m, k, p, R, x) ? GF_ALGO_LEAF : GF_ALGO_STREAM;
+}
+
 // Launch one batch on slot s (called by the dispatcher without the lock held).
 static int launch_batch(gf_server *S, Slot &s, int f) {
     gf_forest *F = S->forests[f];
@@ -111,7 +122,7 @@ static int launch_batch(gf_server *S, Slot &s, int f) {
     o.checks = S->opts.checks;
     o.eps = S->opts.eps;
     o.stream = s.stream;
-    o.algo = GF_ALGO_STREAM;
+    o.algo = batch_algo(S, F, m, k);
     o.workspace = s.ws;
     o.workspace_bytes = s.ws_bytes;
     int r = gf_query_ex(F, s.q_dev, m, k, &o, s.ids_dev, s.d_dev);
@@ -225,7 +236,8 @@ extern "C" int gf_server_create(gf_forest *const *forests, int32_t nforests, con
     gf_server_opts o;
     gf_server_opts_default(&o);
     if (opts) o = *opts;
-    if (o.max_batch < 1 || o.slots < 1 || o.k_max < 1 || o.hbm_budget_bytes <= 0)
+    if (o.max_batch < 1 || o.slots < 1 || o.k_max < 1 || o.hbm_budget_bytes <= 0 ||
+        (o.algo != GF_ALGO_AUTO && o.algo != GF_ALGO_STREAM))
         return gf_fail(GF_EINVAL, "bad server options");
     if (o.precision != GF_FP32 && o.k_max > (o.rerank_R > 0 ? o.rerank_R : 64))
         return gf_fail(GF_EINVAL, "k_max exceeds the shortlist");
@@ -244,11 +256,17 @@ extern "C" int gf_server_create(gf_forest *const *forests, int32_t nforests, con
         qo.rerank_R = o.rerank_R;
         qo.checks = o.checks;
         qo.eps = o.eps;
-        qo.algo = GF_ALGO_STREAM;  // the kernel launch_batch runs
+        qo.algo = GF_ALGO_STREAM;  // the streaming kernel, for any batch
         int64_t b = 0;
         int r = gf_query_workspace_size(forests[i], o.max_batch, &qo, &b);
         if (r) { delete S; return r; }
         ws_max = std::max(ws_max, b);
+        // the leaf-major path, for a full batch if it would take one (its scratch grows with m)
+        if (batch_algo(S, forests[i], o.max_batch, 1) == GF_ALGO_LEAF) {
+            qo.algo = GF_ALGO_LEAF;
+            if ((r = gf_query_workspace_size(forests[i], o.max_batch, &qo, &b))) { delete S; return r; }
+            ws_max = std::max(ws_max, b);
+        }
     }
     const int64_t per_slot = (int64_t)o.max_batch * S->dmax * 4 + (int64_t)o.max_batch * o.k_max * 12 + ws_max;
     const int nslots = (int)std::min<int64_t>(o.slots, o.hbm_budget_bytes / per_slot);

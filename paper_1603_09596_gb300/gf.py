@@ -46,7 +46,7 @@ class QueryOpts(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("slots", C.c_int32), ("hbm_budget_bytes", C.c_int64),
                 ("k_max", C.c_int32), ("precision", C.c_int32), ("rerank_R", C.c_int32),
-                ("checks", C.c_int32), ("eps", C.c_double)]
+                ("checks", C.c_int32), ("eps", C.c_double), ("algo", C.c_int32)]
 
 
 class ServerStats(C.Structure):
@@ -346,10 +346,10 @@ class Server:
 
     def __init__(self, forests, max_batch: int = 1024, slots: int = 4, hbm_budget_bytes: int = 4 << 30,
                  k_max: int = 10, precision: int = GF_FP32, rerank_R: int = 0, checks: int = 0,
-                 eps: float = 0.0):
+                 eps: float = 0.0, algo: int = GF_ALGO_AUTO):
         self.forests = list(forests)      # keep the forests alive while the server runs
         arr = (C.c_void_p * len(self.forests))(*[f.handle for f in self.forests])
-        o = ServerOpts(max_batch, slots, hbm_budget_bytes, k_max, precision, rerank_R, checks, eps)
+        o = ServerOpts(max_batch, slots, hbm_budget_bytes, k_max, precision, rerank_R, checks, eps, algo)
         self.handle = C.c_void_p()
         _check(lib().gf_server_create(arr, len(self.forests), C.byref(o), C.byref(self.handle)))
         self.dims = [f.info.d for f in self.forests]

@@ -1,4 +1,5 @@
-"""Continuous-batching server: every answer equals the query run alone; admission by HBM budget."""
+"""Continuous-batching server: every answer equals the query run alone (streaming kernel) or the
+oracle's search within tolerance (large batches on the leaf-major path); admission by HBM budget."""
 import threading
 
 import numpy as np
@@ -88,7 +89,9 @@ def test_hbm_budget_limits_slots(gf, forests):
     F, _ = forests[2]
     big = gf.Server([F], max_batch=256, slots=8, hbm_budget_bytes=8 << 30)
     assert big.slots == 8
-    one = gf.gf_query_workspace_size(F, 256) + 256 * F.info.d * 4 + 256 * 10 * 12
+    # a slot holds a full batch's queries and results and the larger scratch of the two kernels a
+    # batch may take (the leaf-major path's, when a full batch would take it)
+    one = gf.gf_query_workspace_size(F, 256, algo=gf.GF_ALGO_AUTO) + 256 * F.info.d * 4 + 256 * 10 * 12
     S = gf.Server([F], max_batch=256, slots=8, hbm_budget_bytes=3 * one + 100)
     assert S.slots == 3
     S.close()
@@ -120,3 +123,39 @@ def test_poisson_load_reports_latency(gf, forests):
     assert st["completed"] > 1000
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
     S.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_large_batches_take_the_leaf_path(gf, prec):
+    """A forest of two leaves a tree: batches of 8 queries or more share leaves enough for the
+    leaf-major path (the rule of GF_ALGO_AUTO), which the server then runs; with one slot, requests
+    pile up while a batch runs.  Every answer must be the oracle's search on the same forest, within
+    the tolerance of the kernel that served it."""
+    import oracle
+    from oracle import screen
+    from parity import assert_screened_close, assert_topk_close
+    X, Q = synth.mixture(8000, 64, 1024, "B", seed=31, qseed=32)
+    F = gf.gf_build(torch.from_numpy(X).cuda(), 8, 4000, seed=3)
+    assert F.info.L == 1
+    gf.gf_forest_add_screen(F, gf.GF_BF16_RERANK)
+    p = gf.PRECISIONS[prec]
+    S = gf.Server([F], max_batch=512, slots=1, k_max=10, precision=p, rerank_R=32)
+    tickets = [S.submit(0, Q[i], 10) for i in range(Q.shape[0])]
+    res = [S.poll(t, 10) for t in tickets]
+    st = S.stats()
+    S.close()
+    assert st["mean_batch"] >= 8, st
+    gi = np.stack([r[0] for r in res])
+    gd = np.stack([r[1] for r in res])
+    sd, sv, pm = gf.gf_forest_export(F)
+    inf = F.info
+    Fo = oracle.Forest(inf.n, inf.d, inf.T, inf.leaf_size, inf.L, sd, sv, pm)
+    offs, ids = oracle.candidates(Fo, oracle.descend(Fo, Q))
+    if prec == "fp32":
+        oi, od = oracle.topk(X, Q, offs, ids, 10)
+        assert_topk_close(X, Q, gi, gd, oi, od)
+    else:
+        oi, od, _ = screen.screened_search(Fo, X, Q, 10, 32, "bf16", offs, ids)
+        # the norm form's bound is the wider one: it covers a batch served by either kernel
+        assert_screened_close(X, Q, gi, gd, oi, od, offs, ids, "bf16", 32, "norm")
+    assert gf.gf_kernel_status() == 0
