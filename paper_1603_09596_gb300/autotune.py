@@ -42,7 +42,8 @@ def _time(fn, reps: int = 3) -> float:
 def _recalls(ids: torch.Tensor, dists: torch.Tensor, ex_ids: torch.Tensor, ex_d: torch.Tensor):
     """recall@1 (the first answer at the exact nearest distance; equal distances count, Sec. 4) and
     recall@k of a result against exact neighbours."""
-    r1 = float(((dists[:, 0] <= ex_d[:, 0]) & (ids[:, 0] >= 0)).float().mean())
+    # (float32 distances of the same point from two kernels may differ in the last bits)
+    r1 = float(((dists[:, 0] <= ex_d[:, 0] * (1 + 2e-6)) & (ids[:, 0] >= 0)).float().mean())
     rk = float((ids[:, :, None] == ex_ids[:, None, :]).any(-1).float().mean())
     return r1, rk
 
