@@ -442,7 +442,7 @@ def ours(args):
     tr = recorded_traffic(algo)
     if tr and tr.get("point") != point_id:
         tr = None
-    traffic = tr["bytes_per_launch"] if tr else None
+    traffic = (tr.get("bytes_per_step") or tr.get("bytes_per_launch")) if tr else None
     alg_bytes = best["bytes_per_query"] * m
     if algo == "leaf":
         st = leaf_stats(gf, Fc, Qg, best["R"], k, "bf16")
