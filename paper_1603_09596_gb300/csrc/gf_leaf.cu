@@ -14,11 +14,11 @@
 //      first, then the others by the smallest tree-0 leaf among their queries, so chunks of
 //      different trees that cover the same region of the data run at about the same time and find
 //      each other's rows in L2;
-//   4. score (k_leaf_score): one persistent CTA per SM walks the chunks.  A chunk's leaf rows are
-//      staged in shared memory 128 at a time, in stages of three 64-wide k-steps, each k-step
-//      gathered by its own producer warp, and multiplied against the chunk's queries on the tensor
-//      cores (tcgen05.mma, M = 128 rows, N = the queries' hi and lo parts, bf16 inputs, float32
-//      accumulators in tensor memory, issued by one thread).  The screened
+//   4. score (k_leaf_score): two persistent CTAs per SM walk the chunks.  A chunk's leaf rows are
+//      staged in shared memory 128 at a time through a ring of 128-byte k-slices, each gathered by
+//      its own producer warp, and multiplied against the chunk's queries on the tensor cores
+//      (tcgen05.mma, M = 128 rows, N = the queries' hi and lo parts, bf16 inputs, float32
+//      accumulators in tensor memory, issued by one thread of each CTA).  The screened
 //      score of point x for query q is |x~|^2 - 2 x~.q, which orders the points of one query as
 //      |x~ - q|^2 does (the two differ by |q|^2).  x~ is the bf16 copy of the forest; the query
 //      enters as two bf16 parts hi + lo (hi = bf16(q), lo = bf16(q - hi)), i.e. with about 16
@@ -73,10 +73,13 @@ template <int FMT>
 struct LeafCfg {
     static constexpr int QP = FMT == LF_FP8 ? 3 : 2;       // query parts
     static constexpr int ESZ = FMT == LF_FP8 ? 1 : 2;      // bytes per value
-    // sub-tiles (128-byte k-slices) per stage -- one wait and one release each -- and stages: for
-    // E4M3, four stages of two, a ring of eight k-slices, which a 960-value row fills exactly
-    static constexpr int SUB = FMT == LF_FP8 ? 2 : 3;
-    static constexpr int STAGES = FMT == LF_FP8 ? 4 : 3;
+    // sub-tiles (128-byte k-slices) per stage -- one wait and one release each -- and stages: a
+    // ring of four (bf16) or three (E4M3) k-slices, one producer warp each, so that two CTAs fit
+    // one SM (two MMA issuers and eight epilogue warps per SM: measured faster than one CTA with a
+    // ring of nine or eight)
+    static constexpr int SUB = 1;
+    static constexpr int STAGES = FMT == LF_FP8 ? 3 : 4;
+    static constexpr int CTAS_PER_SM = 2;
     static constexpr int PROD_WARPS = SUB * STAGES;  // producer warps; each loads whole sub-tiles
     static constexpr int A_BYTES = BM * 128;
     static constexpr int B_BYTES = NQ * 128;         // one query part of the chunk
@@ -89,7 +92,9 @@ struct LeafCfg {
     static constexpr int THREADS = (MMA_WARP + 1) * 32;
     // shared-memory plan (offsets from a 1024-aligned base)
     static constexpr int SM_WL = STAGES * STAGE_BYTES;            // the epilogue warps' lists [4][NQ][32]
-    static constexpr int SM_BAR = SM_WL + 4 * NQ * 32 * 8;        // full[STAGES] empty[STAGES] dfull[2] dempty[2] fin
+    static constexpr int SM_SV = SM_WL + 4 * NQ * 32 * 8;         // a tile's x~.q~ [4][NQ][32] (float)
+    static constexpr int SM_THR = SM_SV + 4 * NQ * 32 * 4;        // the lists' bounds [4][NQ]
+    static constexpr int SM_BAR = SM_THR + 4 * NQ * 8;            // full[STAGES] empty[STAGES] dfull[2] dempty[2] fin
     static constexpr int SM_MISC = SM_BAR + (2 * STAGES + 5) * 8; // tensor-memory base, abort flag
     static constexpr int SMEM_BYTES = SM_MISC + 16 + 1024;        // slack for aligning the base
     // instruction descriptor: float32 D, A and B K-major, M = BM, N = MMA_N; bf16 inputs (kind::f16)
@@ -99,6 +104,7 @@ struct LeafCfg {
     static_assert(SUBTILE_BYTES % 1024 == 0, "sub-tiles must keep the 1024-byte swizzle alignment");
     static_assert(MMA_N % 16 == 0 && MMA_N <= ACC_COLS, "MMA shape");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+    static_assert(CTAS_PER_SM * (SMEM_BYTES + 1024) <= 228 * 1024, "shared memory of the CTAs of one SM");
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -347,8 +353,10 @@ __device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A,
     nq = min(NQ, A.bcnt[u] - it.y);
 }
 
+// 96 registers a thread: two CTAs of up to nine warps on one SM, at most five warps on one SM
+// sub-partition (5 * 32 * 96 registers fit its 16,384)
 template <int FMT>
-__global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestView F, LeafArgs A) {
+__global__ void __maxnreg__(96) k_leaf_score(ForestView F, LeafArgs A) {
     using Cfg = LeafCfg<FMT>;
     constexpr int QP = Cfg::QP, SUB = Cfg::SUB, STAGES = Cfg::STAGES, PROD_WARPS = Cfg::PROD_WARPS;
     constexpr int A_BYTES = Cfg::A_BYTES, B_BYTES = Cfg::B_BYTES, SUBTILE_BYTES = Cfg::SUBTILE_BYTES;
@@ -404,8 +412,8 @@ __global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestV
         // arrives on the stage's full barrier: no sub-tile waits for another one's copies.
         // A warp always fills the same ring slot (PROD_WARPS sub-tiles make one turn of the ring), so
         // the query parts it copied last are still there: when a row tile takes exactly one turn of
-        // the ring, every later tile of the chunk finds its k-slice's parts in place and the warp
-        // copies the leaf rows alone.
+        // the ring (a row of as many k-slices as the ring holds), every later tile of the chunk finds
+        // its k-slice's parts in place and the warp copies the leaf rows alone.
         const int pw = warp - 4;
         const int c = lane & 7, r0 = lane >> 3;  // column chunk; rows r0, r0 + 4, ...
         uint32_t it = 0;                          // stages of the CTA's earlier chunks
@@ -519,24 +527,30 @@ __global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestV
     } else {
         // ------------------------------------------------ epilogue: screened keys, R best per query
         // Each warp keeps, for every query of the chunk, the list of the R best keys of its own
-        // 32 rows of every tile; the four lists are merged when the chunk is done.
+        // 32 rows of every tile (in shared memory, with the list's bound: its R-th key or tau_q);
+        // the four lists are merged when the chunk is done.  A tile's scores go through shared
+        // memory too, so that the query loop is a short rolled loop (four queries a turn) and not
+        // one unrolled copy per query.
         const int et = tid;  // tile row and tensor-memory lane
         const int R = A.R;
         int RL = 1;
         while (RL < R) RL <<= 1;
+        float *sv = reinterpret_cast<float *>(sm + Cfg::SM_SV) + warp * NQ * 32;  // [NQ][lane]
+        unsigned long long *sl = wl + warp * NQ * 32;                             // [NQ][lane]
+        unsigned long long *sthr = reinterpret_cast<unsigned long long *>(sm + Cfg::SM_THR) + warp * NQ;
         uint32_t tile = 0;
         bool ok = true;
         for (int w = item_lo + blockIdx.x; w < item_hi; w += gridDim.x) {
             int t, rows, q0pos, nq;
             long long lo;
             chunk_of(F, A, w, t, lo, rows, q0pos, nq);
-            unsigned long long lst[NQ];
-#pragma unroll
-            for (int j = 0; j < NQ; ++j) lst[j] = KEY_NONE;
             // lane j: query j of the chunk, its bound and (E4M3 parts) the scale of its part 0
             const int my_qid = lane < nq ? A.qlist[q0pos + lane] / A.S : 0;
             const unsigned long long my_tau = lane < nq ? __ldcg(A.tau + my_qid) : KEY_NONE;
             const float my_c = FMT == LF_FP8 && lane < nq ? __ldg(A.qc + my_qid) : 1.f;
+            for (int j = 0; j < nq; ++j) sl[j * 32 + lane] = KEY_NONE;
+            if (lane < nq) sthr[lane] = my_tau;
+            __syncwarp();
             const int MT = (rows + BM - 1) / BM;
             for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
                 const int r = mt * BM + et;
@@ -551,7 +565,6 @@ __global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestV
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t ta = tmem_base + ((uint32_t)(warp * 32) << 16) + buf * ACC_COLS;
-                float v[NQ];  // x~ . q~ of the lane's row for every query of the chunk (codes for E4M3)
                 {
                     uint32_t acc[QP][16];
 #pragma unroll
@@ -559,48 +572,60 @@ __global__ void __launch_bounds__(LeafCfg<FMT>::THREADS, 1) k_leaf_score(ForestV
                     tmem_wait();
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
+                        float v;  // x~ . q~ of the lane's row for query i (codes for E4M3)
                         if (FMT == LF_FP8)  // p0 + p1 / 16 + p2 / 256 (exact scalings)
-                            v[i] = __uint_as_float(acc[0][i]) +
-                                   fmaf(__uint_as_float(acc[2][i]), 1.f / 16.f, __uint_as_float(acc[1][i])) *
-                                       (1.f / 16.f);
+                            v = __uint_as_float(acc[0][i]) +
+                                fmaf(__uint_as_float(acc[2][i]), 1.f / 16.f, __uint_as_float(acc[1][i])) * (1.f / 16.f);
                         else
-                            v[i] = __uint_as_float(acc[0][i]) + __uint_as_float(acc[1][i]);
+                            v = __uint_as_float(acc[0][i]) + __uint_as_float(acc[1][i]);
+                        sv[i * 32 + lane] = v;
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(dempty + buf);
+                // the queries four at a time: their keys and ballots first, then the (rare) list
+                // insertions
+                constexpr int QB = 4;
+#pragma unroll 1
+                for (int j0 = 0; j0 < nq; j0 += QB) {
+                    unsigned long long key[QB];
+                    unsigned bl[QB];
 #pragma unroll
-                for (int j = 0; j < NQ; ++j) {
-                    if (j < nq) {
+                    for (int b = 0; b < QB; ++b) {
+                        const int j = min(j0 + b, NQ - 1);
                         // screened score |x~|^2 - 2 x~.q~; for E4M3 -2 s_x c is a power-of-two
                         // multiple of s_x, so the product is exact
                         const float kj = FMT == LF_FP8 ? kx * __shfl_sync(FULL, my_c, j) : kx;
-                        const float s = fmaf(kj, v[j], xn);
-                        const unsigned long long key =
-                            valid ? (((unsigned long long)ord_f32(s) << 32) | (unsigned)id) : KEY_NONE;
-                        const unsigned long long thr =
-                            umin64(__shfl_sync(FULL, lst[j], R - 1), __shfl_sync(FULL, my_tau, j));
-                        const unsigned bl = __ballot_sync(FULL, key < thr);
-                        if (bl) lst[j] = list_add(lst[j], key, bl, R, RL);
+                        const float s = fmaf(kj, sv[j * 32 + lane], xn);
+                        key[b] = valid ? (((unsigned long long)ord_f32(s) << 32) | (unsigned)id) : KEY_NONE;
+                        bl[b] = __ballot_sync(FULL, j0 + b < nq && key[b] < sthr[j]);
+                    }
+#pragma unroll
+                    for (int b = 0; b < QB; ++b) {
+                        if (bl[b]) {
+                            const int j = j0 + b;
+                            const unsigned long long nl = list_add(sl[j * 32 + lane], key[b], bl[b], R, RL);
+                            sl[j * 32 + lane] = nl;
+                            const unsigned long long kth = __shfl_sync(FULL, nl, R - 1);
+                            if (lane == 0) sthr[j] = umin64(sthr[j], kth);
+                            __syncwarp();
+                        }
                     }
                 }
             }
-            // all four warps are done with the chunk (and with the previous chunk's lists)
+            // all four warps are done with the chunk's lists
             if (epi_any(!ok)) break;
-#pragma unroll
-            for (int j = 0; j < NQ; ++j)
-                if (j < nq) wl[(warp * NQ + j) * 32 + lane] = lst[j];
-            epi_sync();
             for (int j = warp; j < nq; j += 4) {
                 unsigned long long a = wl[(0 * NQ + j) * 32 + lane], b = wl[(1 * NQ + j) * 32 + lane];
                 unsigned long long c = wl[(2 * NQ + j) * 32 + lane], d = wl[(3 * NQ + j) * 32 + lane];
                 if (lane >= RL) a = b = c = d = KEY_NONE;
                 const unsigned long long best = warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL);
-                const int pr = A.qlist[q0pos + j];  // q S + slot
+                const int pr = A.qlist[q0pos + j];
                 if (lane < R) A.part[(size_t)pr * R + lane] = best;
                 const unsigned long long kth = __shfl_sync(FULL, best, R - 1);
                 if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + pr / A.S, kth);
             }
+            epi_sync();  // the merges have read the lists before the next chunk resets them
         }
     }
     tc_fence_before();
@@ -1181,9 +1206,9 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
         A.item_hi = wave == 0 ? koff + (1 << F->L) : koff + nk;
         if (f32) k_leaf_f32<<<F->num_sms * f32k::CTAS_PER_SM, f32k::THREADS, f32k::SMEM, st>>>(view_of(F), A);
         else if (f8)
-            k_leaf_score<LF_FP8><<<F->num_sms, LeafCfg<LF_FP8>::THREADS, LeafCfg<LF_FP8>::SMEM_BYTES, st>>>(view_of(F), A);
+            k_leaf_score<LF_FP8><<<F->num_sms * LeafCfg<LF_FP8>::CTAS_PER_SM, LeafCfg<LF_FP8>::THREADS, LeafCfg<LF_FP8>::SMEM_BYTES, st>>>(view_of(F), A);
         else
-            k_leaf_score<LF_BF16><<<F->num_sms, LeafCfg<LF_BF16>::THREADS, LeafCfg<LF_BF16>::SMEM_BYTES, st>>>(view_of(F), A);
+            k_leaf_score<LF_BF16><<<F->num_sms * LeafCfg<LF_BF16>::CTAS_PER_SM, LeafCfg<LF_BF16>::THREADS, LeafCfg<LF_BF16>::SMEM_BYTES, st>>>(view_of(F), A);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major scoring launch");
     if (events && (e = cudaEventRecord(events[1], st)) != cudaSuccess) return fail(e, "cudaEventRecord");
