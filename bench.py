@@ -408,6 +408,10 @@ def ours(args):
                 e["tuning_recall"] = {str(r): v for r, v in tr["recall"].items()}
             if st:
                 e["chunks"] = st["chunks"]
+                if pn != "fp32":  # the autotuner's shape of the tensor-core kernel
+                    e["ctas_per_sm"] = tr["ctas_per_sm"] or 2
+                    e["shape_ms"] = {("1 CTA/SM" if key.split("x")[1] == "1" else "2 CTAs/SM"): round(v, 3)
+                                     for key, v in tr["timings"].items()}
             elif "warps" in tr:
                 e.update(warps_per_cta=tr["warps"], ctas_per_sm=tr["ctas_per_sm"], rows_in_flight=tr["rows_in_flight"])
             entry[name] = e
@@ -440,8 +444,8 @@ def ours(args):
     gal = gf.GF_ALGO_LEAF if algo == "leaf" else gf.GF_ALGO_STREAM
     kms = time_kernel(gf, Fc, Qg, k, gf.GF_BF16_RERANK, gal, best["R"], args.steps, dev, checks=cc)
     tr = recorded_traffic(algo)
-    if tr and tr.get("point") != point_id:
-        tr = None
+    if tr and (tr.get("point") != point_id or tr.get("ctas_per_sm", 2) != best.get("ctas_per_sm", 2)):
+        tr = None  # taken on another workload or kernel shape
     traffic = (tr.get("bytes_per_step") or tr.get("bytes_per_launch")) if tr else None
     alg_bytes = best["bytes_per_query"] * m
     if algo == "leaf":

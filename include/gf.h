@@ -88,7 +88,8 @@ typedef struct gf_query_opts {
     int32_t precision;       /* GF_FP32, GF_BF16_RERANK or GF_FP8_RERANK */
     int32_t rerank_R;        /* shortlist length for the screened precisions; 0 = forest default */
     int32_t warps_per_cta;   /* kernel shape; 0 = forest default (set by gf_forest_set_tuning) */
-    int32_t ctas_per_sm;     /* kernel shape; 0 = forest default, else occupancy limit */
+    int32_t ctas_per_sm;     /* kernel shape; 0 = forest default, else occupancy limit (LEAF with a
+                                screen: 1 = one CTA per SM with a deeper ring, else two) */
     void *stream;            /* cudaStream_t */
     int32_t algo;            /* GF_ALGO_* */
     int32_t rows_in_flight;  /* STREAM only: rows each warp scores at once, 2 or 4; 0 = default */

@@ -2,7 +2,8 @@
 
 For a resident forest and a sample of queries it
   1. times every (warps per CTA, CTAs per SM) shape of the query kernel in each precision and
-     keeps the fastest;
+     keeps the fastest (the leaf-major tensor-core kernel: one or two CTAs per SM, i.e. a ring of
+     eight or nine k-slices per SM against two rings of three or four);
   2. for a screened precision, picks the shortest shortlist R that costs the search no accuracy
      (the screen only decides which candidates get the exact float32 rerank, so this is what R
      trades away): given the points X, the shortest R whose recall@1 and recall@10 on the sample,
@@ -90,7 +91,9 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
         res["R"] = R
     timings = {}
     if algo == gf.GF_ALGO_LEAF:
-        shapes = [(inf_w, 0, 0) for inf_w in (8,)]  # the leaf-major kernels have one shape
+        # the leaf-major tensor-core kernel: two CTAs per SM (0, the default) or one with a deeper
+        # ring (1); the float32 one has a single shape
+        shapes = [(8, 0, 0)] + ([(8, 1, 0)] if precision != gf.GF_FP32 else [])
     for w, c, g in shapes:
         try:
             t = _time(lambda: gf.gf_query(F, Q, k, precision=precision, rerank_R=R, warps_per_cta=w,

@@ -168,9 +168,11 @@ inline int32_t leaf_budget_of(const gf_forest *F, int32_t checks, double eps) {
 
 // Leaf-major batched path (GF_ALGO_LEAF): float32 or the bf16 screen.
 // leaf_budget > 0: the priority search's leaves (QueryExtra::leaf_budget), else one leaf per tree.
+// ctas_per_sm: the tensor-core kernel's shape, 1 = one CTA per SM (deeper ring), else two.
 int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision, int32_t R,
                    int32_t order, int32_t leaf_budget, cudaStream_t st, int64_t *ids, float *dists,
-                   void *workspace, int64_t workspace_bytes, cudaEvent_t *events = nullptr);
+                   void *workspace, int64_t workspace_bytes, cudaEvent_t *events = nullptr,
+                   int32_t ctas_per_sm = 0);
 int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order,
                                 int32_t leaf_budget);
 // Whether GF_ALGO_AUTO takes the leaf-major path for this batch.

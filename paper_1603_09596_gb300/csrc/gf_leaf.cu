@@ -69,17 +69,22 @@ constexpr int MAX_KEYS = 8192;   // T * R limit of the merge
 //         K = 32 per MMA, so a row tile takes half the instructions and half the bytes.
 constexpr int LF_BF16 = 0, LF_FP8 = 1;
 
-template <int FMT>
+// CPS: CTAs per SM, the kernel's shape (the autotuner's choice per forest and precision)
+template <int FMT, int CPS = 2>
 struct LeafCfg {
     static constexpr int QP = FMT == LF_FP8 ? 3 : 2;       // query parts
     static constexpr int ESZ = FMT == LF_FP8 ? 1 : 2;      // bytes per value
-    // sub-tiles (128-byte k-slices) per stage -- one wait and one release each -- and stages: a
-    // ring of four (bf16) or three (E4M3) k-slices, one producer warp each, so that two CTAs fit
-    // one SM (two MMA issuers and eight epilogue warps per SM: measured faster than one CTA with a
-    // ring of nine or eight)
-    static constexpr int SUB = 1;
-    static constexpr int STAGES = FMT == LF_FP8 ? 3 : 4;
-    static constexpr int CTAS_PER_SM = 2;
+    // sub-tiles (128-byte k-slices) per stage -- one wait and one release each -- and stages, one
+    // producer warp per sub-tile of the ring.  Two CTAs per SM (two MMA issuers and eight epilogue
+    // warps per SM): rings of four (bf16) or three (E4M3) k-slices, 96 registers a thread.  One CTA
+    // per SM: rings of nine (3 x 3, bf16) or eight (4 x 2, E4M3; a 960-value row fills it exactly),
+    // 128 registers a thread.
+    static constexpr int SUB = CPS == 2 ? 1 : FMT == LF_FP8 ? 2 : 3;
+    static constexpr int STAGES = CPS == 2 ? (FMT == LF_FP8 ? 3 : 4) : FMT == LF_FP8 ? 4 : 3;
+    static constexpr int CTAS_PER_SM = CPS;
+    // registers a thread: at most 65,536 / (CTAs x threads) and, per SM sub-partition (16,384
+    // registers, every fourth warp of a CTA), 5 * 32 * 96 or 4 * 32 * 128
+    static constexpr int REGS = CPS == 2 ? 96 : 128;
     static constexpr int PROD_WARPS = SUB * STAGES;  // producer warps; each loads whole sub-tiles
     static constexpr int A_BYTES = BM * 128;
     static constexpr int B_BYTES = NQ * 128;         // one query part of the chunk
@@ -105,6 +110,9 @@ struct LeafCfg {
     static_assert(MMA_N % 16 == 0 && MMA_N <= ACC_COLS, "MMA shape");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
     static_assert(CTAS_PER_SM * (SMEM_BYTES + 1024) <= 228 * 1024, "shared memory of the CTAs of one SM");
+    static_assert(CPS == 1 || CPS == 2, "one or two CTAs per SM");
+    static_assert(CTAS_PER_SM * THREADS * REGS <= 65536, "registers of the CTAs of one SM");
+    static_assert((CTAS_PER_SM * THREADS / 32 + 3) / 4 * 32 * REGS <= 16384, "registers of one SM sub-partition");
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -353,11 +361,9 @@ __device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A,
     nq = min(NQ, A.bcnt[u] - it.y);
 }
 
-// 96 registers a thread: two CTAs of up to nine warps on one SM, at most five warps on one SM
-// sub-partition (5 * 32 * 96 registers fit its 16,384)
-template <int FMT>
-__global__ void __maxnreg__(96) k_leaf_score(ForestView F, LeafArgs A) {
-    using Cfg = LeafCfg<FMT>;
+template <int FMT, int CPS>
+__global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F, LeafArgs A) {
+    using Cfg = LeafCfg<FMT, CPS>;
     constexpr int QP = Cfg::QP, SUB = Cfg::SUB, STAGES = Cfg::STAGES, PROD_WARPS = Cfg::PROD_WARPS;
     constexpr int A_BYTES = Cfg::A_BYTES, B_BYTES = Cfg::B_BYTES, SUBTILE_BYTES = Cfg::SUBTILE_BYTES;
     constexpr int STAGE_BYTES = Cfg::STAGE_BYTES, MMA_WARP = Cfg::MMA_WARP, ACC_COLS = Cfg::ACC_COLS;
@@ -1064,6 +1070,18 @@ LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int S, int R, int or
 
 int order_of(int order) { return order == GF_ORDER_GIVEN ? GF_ORDER_GIVEN : GF_ORDER_LOCALITY; }
 
+template <int FMT, int CPS>
+cudaError_t leaf_smem_attr() {
+    return cudaFuncSetAttribute(k_leaf_score<FMT, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                LeafCfg<FMT, CPS>::SMEM_BYTES);
+}
+
+template <int FMT, int CPS>
+void launch_score(const gf_forest *F, const LeafArgs &A, cudaStream_t st) {
+    using Cfg = LeafCfg<FMT, CPS>;
+    k_leaf_score<FMT, CPS><<<F->num_sms * Cfg::CTAS_PER_SM, Cfg::THREADS, Cfg::SMEM_BYTES, st>>>(view_of(F), A);
+}
+
 }  // namespace
 
 const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R,
@@ -1108,7 +1126,7 @@ int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision
 
 int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int32_t precision, int32_t R,
                    int32_t order, int32_t leaf_budget, cudaStream_t st, int64_t *ids, float *dists,
-                   void *workspace, int64_t workspace_bytes, cudaEvent_t *events) {
+                   void *workspace, int64_t workspace_bytes, cudaEvent_t *events, int32_t ctas_per_sm) {
     order = order_of(order);
     const bool f32 = precision == GF_FP32;
     if (f32) R = k;  // the exact distances: the k best of every (query, leaf) suffice
@@ -1178,11 +1196,12 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
                                                   (__nv_bfloat16 *)(qpart + W.qpart_stride));
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major regrouping");
 
+    // the tensor-core kernel's shape: one CTA per SM when the caller or the forest's tuning asks for
+    // exactly one, else two
+    const int cps = ctas_per_sm == 1 ? 1 : 2;
     e = f32 ? cudaFuncSetAttribute(k_leaf_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, f32k::SMEM)
-        : f8 ? cudaFuncSetAttribute(k_leaf_score<LF_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    LeafCfg<LF_FP8>::SMEM_BYTES)
-             : cudaFuncSetAttribute(k_leaf_score<LF_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    LeafCfg<LF_BF16>::SMEM_BYTES);
+        : f8 ? (cps == 1 ? leaf_smem_attr<LF_FP8, 1>() : leaf_smem_attr<LF_FP8, 2>())
+             : (cps == 1 ? leaf_smem_attr<LF_BF16, 1>() : leaf_smem_attr<LF_BF16, 2>());
     if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(leaf-major scoring)");
     LeafArgs A;
     A.items = items;
@@ -1205,10 +1224,8 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
         A.item_lo = wave == 0 ? koff : koff + (1 << F->L);
         A.item_hi = wave == 0 ? koff + (1 << F->L) : koff + nk;
         if (f32) k_leaf_f32<<<F->num_sms * f32k::CTAS_PER_SM, f32k::THREADS, f32k::SMEM, st>>>(view_of(F), A);
-        else if (f8)
-            k_leaf_score<LF_FP8><<<F->num_sms * LeafCfg<LF_FP8>::CTAS_PER_SM, LeafCfg<LF_FP8>::THREADS, LeafCfg<LF_FP8>::SMEM_BYTES, st>>>(view_of(F), A);
-        else
-            k_leaf_score<LF_BF16><<<F->num_sms * LeafCfg<LF_BF16>::CTAS_PER_SM, LeafCfg<LF_BF16>::THREADS, LeafCfg<LF_BF16>::SMEM_BYTES, st>>>(view_of(F), A);
+        else if (f8) cps == 1 ? launch_score<LF_FP8, 1>(F, A, st) : launch_score<LF_FP8, 2>(F, A, st);
+        else cps == 1 ? launch_score<LF_BF16, 1>(F, A, st) : launch_score<LF_BF16, 2>(F, A, st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major scoring launch");
     if (events && (e = cudaEventRecord(events[1], st)) != cudaSuccess) return fail(e, "cudaEventRecord");

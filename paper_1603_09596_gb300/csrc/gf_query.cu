@@ -864,7 +864,7 @@ int gf_launch_query(const gf_forest *F, const float *Q, int64_t m, int32_t k, in
         const char *why = gf_leaf_unsupported(F, m, k, precision, R, x);
         if (why) return gf_fail(GF_EUNSUPPORTED, "GF_ALGO_LEAF: %s", why);
         return gf_launch_leaf(F, Q, m, k, precision, R, x.order, x.leaf_budget, st, ids, dists, x.workspace,
-                              x.workspace_bytes, x.events);
+                              x.workspace_bytes, x.events, ctas_per_sm);
     }
     switch (precision) {
         case GF_FP32: return dispatch_prec<P_F32>(F, Q, m, k, R, warps, ctas_per_sm, st, ids, dists, x);

@@ -84,6 +84,25 @@ def test_leaf_matches_oracle(gf, name, R, prec):
     assert gf.gf_kernel_status() == 0
 
 
+@pytest.mark.parametrize("name", ["ragged", "long_rows", "shared", "crowded"])
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_leaf_one_cta_shape_matches_oracle(gf, name, prec):
+    # the kernel's other shape (one CTA per SM, a deeper ring of k-slices): the oracle's answer
+    # within the screen's bound, and bit for bit the default shape's answer (the shortlist of every
+    # (query, leaf) is the same set whatever order the chunks ran in)
+    X, Q, F = case(name)
+    G = gpu_forest(gf, X, F)
+    k, R = 10, 32
+    Qg = torch.from_numpy(Q).cuda()
+    p = gf.PRECISIONS[prec]
+    gi, gd = gf.gf_query(G, Qg, k, precision=p, rerank_R=R, algo=gf.GF_ALGO_LEAF, ctas_per_sm=1)
+    di, dd = gf.gf_query(G, Qg, k, precision=p, rerank_R=R, algo=gf.GF_ALGO_LEAF)
+    oi, od, cands = oracle_screen(F, X, Q, k, R, prec)
+    assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, *cands, prec, R, "norm")
+    assert torch.equal(gi, di) and torch.equal(gd, dd)
+    assert gf.gf_kernel_status() == 0
+
+
 @pytest.mark.parametrize("k,R", [(1, 1), (1, 16), (5, 16), (7, 7)])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_leaf_small_k(gf, k, R, prec):
