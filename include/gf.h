@@ -374,7 +374,7 @@ typedef struct gf_server_stats {
     double span_s;        /* first submission to last completion */
     double qps;           /* completed / span_s */
     int32_t slots;
-    int32_t reserved;
+    int32_t leaf_batches; /* batches that ran the leaf-major path (capped at INT32_MAX) */
 } gf_server_stats;
 
 void gf_server_opts_default(gf_server_opts *o);

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -58,6 +59,7 @@ struct Slot {
     bool inflight = false;
     int status = GF_OK;
     int k = 0;
+    int algo = GF_ALGO_STREAM;  // the kernel path of the batch in flight
     std::vector<Request *> batch;
 };
 
@@ -79,7 +81,7 @@ struct gf_server {
     uint64_t next_ticket = 1;
     // statistics
     std::vector<double> lat_ms;
-    uint64_t batches = 0, batched_queries = 0, completed = 0;
+    uint64_t batches = 0, batched_queries = 0, completed = 0, leaf_batches = 0;
     Clock::time_point t_first, t_last;
     bool any = false;
 };
@@ -123,6 +125,7 @@ static int launch_batch(gf_server *S, Slot &s, int f) {
     o.eps = S->opts.eps;
     o.stream = s.stream;
     o.algo = batch_algo(S, F, m, k);
+    s.algo = o.algo;
     o.workspace = s.ws;
     o.workspace_bytes = s.ws_bytes;
     int r = gf_query_ex(F, s.q_dev, m, k, &o, s.ids_dev, s.d_dev);
@@ -166,6 +169,7 @@ static void dispatcher_loop(gf_server *S, int device) {
         s.status = r;
         s.inflight = true;
         S->batches++;
+        S->leaf_batches += s.algo == GF_ALGO_LEAF;
         S->batched_queries += s.batch.size();
         S->cv_inflight.notify_one();
     }
@@ -371,6 +375,7 @@ extern "C" int gf_server_get_stats(gf_server *S, gf_server_stats *st) {
     st->span_s = S->any ? std::chrono::duration<double>(S->t_last - S->t_first).count() : 0.0;
     st->qps = st->span_s > 0 ? st->completed / st->span_s : 0.0;
     st->slots = (int32_t)S->slots.size();
+    st->leaf_batches = (int32_t)std::min<uint64_t>(S->leaf_batches, INT32_MAX);
     return GF_OK;
 }
 
@@ -378,7 +383,7 @@ extern "C" int gf_server_reset_stats(gf_server *S) {
     if (!S) return gf_fail(GF_EINVAL, "null server");
     std::lock_guard<std::mutex> g(S->mu);
     S->lat_ms.clear();
-    S->batches = S->batched_queries = S->completed = 0;
+    S->batches = S->batched_queries = S->completed = S->leaf_batches = 0;
     S->any = false;
     return GF_OK;
 }

@@ -53,10 +53,10 @@ class ServerStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("batches", C.c_int64), ("mean_batch", C.c_double),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
                 ("span_s", C.c_double), ("qps", C.c_double), ("slots", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("leaf_batches", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class ForestInfo(C.Structure):

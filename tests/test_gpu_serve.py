@@ -70,6 +70,7 @@ def test_alone_equals_mixed(gf, forests, prec):
         assert np.array_equal(ids, alone[key][0]) and np.array_equal(d, alone[key][1])
     st = S.stats()
     assert st["completed"] > 0 and st["p99_ms"] >= st["p50_ms"] > 0
+    assert st["leaf_batches"] == 0  # batches of at most 16 share no leaves: all streamed
     S.close()
 
 
@@ -145,6 +146,7 @@ def test_large_batches_take_the_leaf_path(gf, prec):
     st = S.stats()
     S.close()
     assert st["mean_batch"] >= 8, st
+    assert st["leaf_batches"] >= 1, st  # the server says which path its batches took
     gi = np.stack([r[0] for r in res])
     gd = np.stack([r[1] for r in res])
     sd, sv, pm = gf.gf_forest_export(F)
