@@ -258,37 +258,46 @@ def query_bytes(gf, F, prec, C, R, d, k, leaves=0):
 QP = {"fp32": 0, "bf16": 2, "fp8": 3}  # query parts of the tensor-core screens (MMA N = 16 QP)
 
 
-def leaf_stats(gf, F, Qg, R, k, prec):
-    """One leaf-major step, from the batch's own descent: chunks (a (tree, leaf) bucket cut into
-    groups of at most 16 queries), 128-row tiles, (row, query) pairs scored, MMAs issued, and the
-    algorithmic bytes -- every chunk reads its leaf's rows once (the screen's copy with its ids and
-    |x~|^2, and the E4M3 row scale), plus the queries (read, split), the (query, tree) lists written
-    and merged, the float32 rerank rows and the results.  The query parts re-read per row tile come
-    from L2 and are not counted."""
+def leaf_stats(gf, F, Qg, R, k, prec, checks=0):
+    """One leaf-major step, from the batch's own leaves (the descents, or the priority search's
+    lists with `checks`): chunks (a (tree, leaf) bucket cut into groups of at most 16 queries),
+    128-row tiles (two chunks a tile when no leaf exceeds 64 rows), (row, query) pairs scored, MMAs
+    issued, and the algorithmic bytes -- every chunk reads its leaf's rows once (the screen's copy
+    with its ids and |x~|^2, and the E4M3 row scale), plus the queries (read, split), the (query,
+    leaf) lists written and merged, the float32 rerank rows and the results.  The query parts
+    re-read per row tile come from L2 and are not counted."""
     import torch
     inf = F.info
     m, T, L, n, d = Qg.shape[0], inf.T, inf.L, inf.n, inf.d
-    leaf = gf.gf_descend(F, Qg).long()
-    u = (leaf + (torch.arange(T, device=Qg.device) << L)).flatten()
+    if checks:
+        codes, nl = gf.gf_prio_leaves(F, Qg, checks)
+        S = codes.shape[1]
+        live = torch.arange(S, device=Qg.device)[None, :] < nl[:, None]
+        u = codes.long()[live]
+    else:
+        S = T
+        leaf = gf.gf_descend(F, Qg).long()
+        u = (leaf + (torch.arange(T, device=Qg.device) << L)).flatten()
     cnt = torch.bincount(u, minlength=T << L)
     chunks = (cnt + 15) // 16
     b = torch.arange(T << L, device=Qg.device) & ((1 << L) - 1)
     rows = ((b + 1) * n >> L) - (b * n >> L)
-    tiles = int((chunks * ((rows + 127) // 128)).sum())
+    ch = 2 if (n + (1 << L) - 1) >> L <= 64 else 1
+    tiles = int((chunks * ((rows + 127) // 128)).sum()) if ch == 1 else (int(chunks.sum()) + 1) // 2
     pairs = int((cnt * rows).sum())
     ldx, ldb, ld8 = (d + 3) // 4 * 4, (d + 7) // 8 * 8, (d + 15) // 16 * 16
     crow = int((chunks * rows).sum())
     if prec == "fp32":
-        row_b, other = ldx * 4 + 4, m * d * 4 + m * ldx * 4 * 2 + m * T * k * 8 * 2 + m * k * 12
+        row_b, other = ldx * 4 + 4, m * d * 4 + m * ldx * 4 * 2 + m * S * k * 8 * 2 + m * k * 12
     else:
         row_b = (ldb * 2 + 8) if prec == "bf16" else (ld8 + 12)
         qb = ldb * 2 if prec == "bf16" else ld8
-        other = m * d * 4 * 2 + m * qb * QP[prec] + m * T * R * 8 * 2 + m * R * ldx * 4 + m * k * 12
+        other = m * d * 4 * 2 + m * qb * QP[prec] + m * S * R * 8 * 2 + m * R * ldx * 4 + m * k * 12
     esz = {"bf16": 2, "fp8": 1}.get(prec, 4)
     mmas_per_tile = -(-d * esz // 32)  # one MMA per 32 bytes of the row (K = 16 bf16 or 32 E4M3)
-    return {"chunks": int(chunks.sum()), "tiles": tiles, "pairs": pairs, "bytes": crow * row_b + other,
-            "useful_flops": 2.0 * pairs * d * QP[prec],
-            "issued_flops": 2.0 * tiles * 128 * 16 * QP[prec] * mmas_per_tile * (32 // esz) if QP[prec] else 0.0}
+    return {"chunks": int(chunks.sum()), "tiles": tiles, "chunks_per_tile": ch, "pairs": pairs,
+            "bytes": crow * row_b + other, "useful_flops": 2.0 * pairs * d * QP[prec],
+            "issued_flops": 2.0 * tiles * 128 * 16 * ch * QP[prec] * mmas_per_tile * (32 // esz) if QP[prec] else 0.0}
 
 
 def time_kernel(gf, F, Qg, k, prec, algo, R, steps, dev, checks=0):
@@ -382,21 +391,24 @@ def ours(args):
         entry["cand_per_query"] = round(C, 1)
         leaves = gf.leaf_budget(F, checks) if checks else 0
         runs = [("fp32_stream", "fp32", gf.GF_ALGO_STREAM), ("bf16_stream", "bf16", gf.GF_ALGO_STREAM)]
-        if not checks:  # the leaf-major path runs the one-leaf-per-tree search
-            runs += [("fp32_leaf", "fp32", gf.GF_ALGO_LEAF), ("bf16_leaf", "bf16", gf.GF_ALGO_LEAF),
-                     ("fp8_leaf", "fp8", gf.GF_ALGO_LEAF)]
+        # the leaf-major path: one leaf per tree, or the priority search's lists (the screens; its
+        # float32 kernel's 256-row tiles would stay mostly empty on the priority search's small leaves)
+        runs += ([("fp32_leaf", "fp32", gf.GF_ALGO_LEAF)] if not checks else []) + \
+            [("bf16_leaf", "bf16", gf.GF_ALGO_LEAF), ("fp8_leaf", "fp8", gf.GF_ALGO_LEAF)]
         for name, pn, algo in runs:
             prec = gf.PRECISIONS[pn]
             # kernel shape and shortlist: R is the shortest whose recall@1 and recall@10 on the tuning
-            # sample stay within 0.5 points of the float32 search's (the leaf-major path keeps at most 32)
+            # sample stay within 0.5 points of the float32 search's (the leaf-major path keeps at most
+            # 32, and its merge at most 8192 keys a query: (leaves per query) x R); the shape is the
+            # fastest on the whole batch
             tr = autotune.tune(F, Qg[:tune_sample], k, prec, checks=checks, X=Xg, algo=algo,
-                               r_max=32 if algo == gf.GF_ALGO_LEAF else 0)
+                               r_max=min(32, 8192 // max(leaves, T)) if algo == gf.GF_ALGO_LEAF else 0, Qt=Qg)
             R = tr.get("R", 0)
             ids, dd, ms, ck = time_batch(gf, F, Qg, k, prec, args.steps, args.warmup, dev, world, local,
                                          args.no_graph, checks, algo=algo, R=R)
             mean_ms = statistics.mean(ms)
             if algo == gf.GF_ALGO_LEAF:
-                st = leaf_stats(gf, F, Qg, R if pn != "fp32" else k, k, pn)
+                st = leaf_stats(gf, F, Qg, R if pn != "fp32" else k, k, pn, checks)
                 bpq = st["bytes"] / m
             else:
                 st, bpq = None, bytes_per_query(F, prec, C, R, leaves)
@@ -462,7 +474,7 @@ def ours(args):
     traffic = (tr.get("bytes_per_step") or tr.get("bytes_per_launch")) if tr else None
     alg_bytes = best["bytes_per_query"] * m
     if algo == "leaf":
-        st = leaf_stats(gf, Fc, Qg, best["R"], k, "bf16")
+        st = leaf_stats(gf, Fc, Qg, best["R"], k, "bf16", cc)
         kernel = ("k_leaf_score<bf16> (tcgen05 kind::f16 screen; 2 launches per step: the chunks of tree 0, then the "
                   "rest), timed alone; bytes and flops of those launches")
         per_query = bytes_per_query(Fc, gf.GF_BF16_RERANK, chosen["cand_per_query"], best["R"])

@@ -51,9 +51,14 @@ def _recalls(ids: torch.Tensor, dists: torch.Tensor, ex_ids: torch.Tensor, ex_d:
 
 def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0.995,
          shapes=SHAPES, r_choices=R_CHOICES, checks: int = 0, X: torch.Tensor | None = None,
-         tol: float = 0.005, algo: int = gf.GF_ALGO_AUTO, r_max: int = 0) -> dict:
+         tol: float = 0.005, algo: int = gf.GF_ALGO_AUTO, r_max: int = 0,
+         Qt: torch.Tensor | None = None) -> dict:
+    """Qt: the batch the shapes are timed on (default Q); the best shape depends on how many
+    queries share a leaf, so time it on a batch of the size that will run."""
     inf = F.info
-    key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0], checks, X is not None, algo, r_max)
+    Qt = Q if Qt is None else Qt
+    key = (inf.n, inf.d, inf.T, inf.leaf_size, k, precision, Q.shape[0], checks, X is not None, algo, r_max,
+           Qt.shape[0])
     if key in _cache:
         res = _cache[key]
         gf.gf_forest_set_tuning(F, precision, res["warps"], res["ctas_per_sm"], res.get("R", 0),
@@ -96,7 +101,7 @@ def tune(F: gf.Forest, Q: torch.Tensor, k: int, precision: int, agree: float = 0
         shapes = [(8, 0, 0)] + ([(8, 1, 0)] if precision != gf.GF_FP32 else [])
     for w, c, g in shapes:
         try:
-            t = _time(lambda: gf.gf_query(F, Q, k, precision=precision, rerank_R=R, warps_per_cta=w,
+            t = _time(lambda: gf.gf_query(F, Qt, k, precision=precision, rerank_R=R, warps_per_cta=w,
                                           ctas_per_sm=c, rows_in_flight=g, checks=checks, algo=algo))
         except gf.GFError:
             continue

@@ -18,7 +18,9 @@
 //      staged in shared memory 128 at a time through a ring of 128-byte k-slices, each gathered by
 //      its own producer warp, and multiplied against the chunk's queries on the tensor cores
 //      (tcgen05.mma, M = 128 rows, N = the queries' hi and lo parts, bf16 inputs, float32
-//      accumulators in tensor memory, issued by one thread of each CTA).  The screened
+//      accumulators in tensor memory, issued by one thread of each CTA).  Leaves of at most 64
+//      rows (the paper's leaf sizes, and the priority search's) pair up: two chunks share each row
+//      tile, each with its own queries in the B operand.  The screened
 //      score of point x for query q is |x~|^2 - 2 x~.q, which orders the points of one query as
 //      |x~ - q|^2 does (the two differ by |q|^2).  x~ is the bf16 copy of the forest; the query
 //      enters as two bf16 parts hi + lo (hi = bf16(q), lo = bf16(q - hi)), i.e. with about 16
@@ -69,29 +71,39 @@ constexpr int MAX_KEYS = 8192;   // T * R limit of the merge
 //         K = 32 per MMA, so a row tile takes half the instructions and half the bytes.
 constexpr int LF_BF16 = 0, LF_FP8 = 1;
 
-// CPS: CTAs per SM, the kernel's shape (the autotuner's choice per forest and precision)
-template <int FMT, int CPS = 2>
+// CPS: CTAs per SM, the kernel's shape (the autotuner's choice per forest and precision).
+// CH: chunks per row tile.  Leaves of at most 64 rows (the paper's leaf sizes) would fill half a
+// 128-row tile, so two chunks share every tile: rows 0-63 are one chunk's leaf, 64-127 the other's,
+// and the B operand holds both chunks' queries (N doubles; an M = 128 MMA costs the same up to
+// N = 64).  Each epilogue warp scores its rows against its own chunk's queries only.
+template <int FMT, int CPS = 2, int CH = 1>
 struct LeafCfg {
     static constexpr int QP = FMT == LF_FP8 ? 3 : 2;       // query parts
     static constexpr int ESZ = FMT == LF_FP8 ? 1 : 2;      // bytes per value
+    static constexpr int NQT = NQ * CH;                    // query rows of a part in a tile
+    static constexpr int ROWS_PER = BM / CH;               // tile rows of one chunk
+    static constexpr int LW = 4 / CH;                      // epilogue warps (lists) per chunk
     // sub-tiles (128-byte k-slices) per stage -- one wait and one release each -- and stages, one
     // producer warp per sub-tile of the ring.  Two CTAs per SM (two MMA issuers and eight epilogue
     // warps per SM): rings of four (bf16) or three (E4M3) k-slices, 96 registers a thread.  One CTA
     // per SM: rings of nine (3 x 3, bf16) or eight (4 x 2, E4M3; a 960-value row fills it exactly),
     // 128 registers a thread.
-    static constexpr int SUB = CPS == 2 ? 1 : FMT == LF_FP8 ? 2 : 3;
-    static constexpr int STAGES = CPS == 2 ? (FMT == LF_FP8 ? 3 : 4) : FMT == LF_FP8 ? 4 : 3;
+    // With two chunks a tile (sub-tiles of 24 or 28 KB): rings of three (two CTAs) or of eight
+    // (bf16) / seven (E4M3) k-slices (one CTA).
+    static constexpr int SUB = CH == 2 || CPS == 2 ? 1 : FMT == LF_FP8 ? 2 : 3;
+    static constexpr int STAGES = CH == 2 ? (CPS == 2 ? 3 : FMT == LF_FP8 ? 7 : 8)
+                                          : CPS == 2 ? (FMT == LF_FP8 ? 3 : 4) : FMT == LF_FP8 ? 4 : 3;
     static constexpr int CTAS_PER_SM = CPS;
     // registers a thread: at most 65,536 / (CTAs x threads) and, per SM sub-partition (16,384
     // registers, every fourth warp of a CTA), 5 * 32 * 96 or 4 * 32 * 128
     static constexpr int REGS = CPS == 2 ? 96 : 128;
     static constexpr int PROD_WARPS = SUB * STAGES;  // producer warps; each loads whole sub-tiles
     static constexpr int A_BYTES = BM * 128;
-    static constexpr int B_BYTES = NQ * 128;         // one query part of the chunk
+    static constexpr int B_BYTES = NQT * 128;        // one query part of the tile's chunks
     static constexpr int SUBTILE_BYTES = A_BYTES + QP * B_BYTES;  // leaf rows, then the parts
     static constexpr int STAGE_BYTES = SUB * SUBTILE_BYTES;
-    static constexpr int MMA_N = QP * NQ;            // the parts side by side
-    static constexpr int ACC_COLS = 64;              // columns per accumulator (MMA_N <= 64)
+    static constexpr int MMA_N = QP * NQT;           // the parts side by side
+    static constexpr int ACC_COLS = MMA_N <= 64 ? 64 : 128;  // columns per accumulator
     static constexpr int TMEM_COLS = 2 * ACC_COLS;   // two accumulators
     static constexpr int MMA_WARP = 4 + PROD_WARPS;  // warps 4 .. 3 + PROD_WARPS load
     static constexpr int THREADS = (MMA_WARP + 1) * 32;
@@ -107,7 +119,8 @@ struct LeafCfg {
     static constexpr uint32_t IDESC = (1u << 4) | (FMT == LF_BF16 ? (1u << 7) | (1u << 10) : 0u) |
                                       ((uint32_t)(MMA_N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     static_assert(SUBTILE_BYTES % 1024 == 0, "sub-tiles must keep the 1024-byte swizzle alignment");
-    static_assert(MMA_N % 16 == 0 && MMA_N <= ACC_COLS, "MMA shape");
+    static_assert(MMA_N % 16 == 0 && MMA_N <= ACC_COLS && MMA_N <= 256, "MMA shape");
+    static_assert(CH == 1 || CH == 2, "one or two chunks a tile");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
     static_assert(CTAS_PER_SM * (SMEM_BYTES + 1024) <= 228 * 1024, "shared memory of the CTAs of one SM");
     static_assert(CPS == 1 || CPS == 2, "one or two CTAs per SM");
@@ -217,9 +230,9 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
                  "l"(a + 2 * i), "l"(b + 2 * i), "r"(i > 0 ? 1u : accumulate), "r"(idesc)                   \
                  : "memory")
 
-template <int FMT>
+template <int FMT, int CH>
 __device__ __forceinline__ void mma_slice(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate, int nk) {
-    constexpr uint32_t idesc = LeafCfg<FMT>::IDESC;
+    constexpr uint32_t idesc = LeafCfg<FMT, 2, CH>::IDESC;
     if (nk >= 4) {
         if constexpr (FMT == LF_FP8) GF_MMA4("f8f6f4");
         else GF_MMA4("f16");
@@ -361,9 +374,10 @@ __device__ __forceinline__ void chunk_of(const ForestView &F, const LeafArgs &A,
     nq = min(NQ, A.bcnt[u] - it.y);
 }
 
-template <int FMT, int CPS>
-__global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F, LeafArgs A) {
-    using Cfg = LeafCfg<FMT, CPS>;
+template <int FMT, int CPS, int CH>
+__global__ void __maxnreg__((LeafCfg<FMT, CPS, CH>::REGS)) k_leaf_score(ForestView F, LeafArgs A) {
+    using Cfg = LeafCfg<FMT, CPS, CH>;
+    constexpr int NQT = Cfg::NQT, ROWS_PER = Cfg::ROWS_PER, LW = Cfg::LW;
     constexpr int QP = Cfg::QP, SUB = Cfg::SUB, STAGES = Cfg::STAGES, PROD_WARPS = Cfg::PROD_WARPS;
     constexpr int A_BYTES = Cfg::A_BYTES, B_BYTES = Cfg::B_BYTES, SUBTILE_BYTES = Cfg::SUBTILE_BYTES;
     constexpr int STAGE_BYTES = Cfg::STAGE_BYTES, MMA_WARP = Cfg::MMA_WARP, ACC_COLS = Cfg::ACC_COLS;
@@ -422,20 +436,27 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
         // its k-slice's parts in place and the warp copies the leaf rows alone.
         const int pw = warp - 4;
         const int c = lane & 7, r0 = lane >> 3;  // column chunk; rows r0, r0 + 4, ...
-        uint32_t it = 0;                          // stages of the CTA's earlier chunks
+        uint32_t it = 0;                          // stages of the CTA's earlier units
         bool ok = true;
-        int held_w = -1, held_k = -1;             // chunk and k-slice of the query parts in the slot
-        for (int w = item_lo + blockIdx.x; w < item_hi && ok; w += gridDim.x) {
-            int t, rows, q0pos, nq;
-            long long lo;
-            chunk_of(F, A, w, t, lo, rows, q0pos, nq);
-            int qid[NQ / 4];
+        int held_w = -1, held_k = -1;             // unit and k-slice of the query parts in the slot
+        // a unit: the CH consecutive chunks item_lo + wu CH + (0 .. CH-1) that share its row tiles
+        for (int wu = blockIdx.x; item_lo + wu * CH < item_hi && ok; wu += gridDim.x) {
+            int t[CH], rows[CH], q0pos[CH], nq[CH];
+            long long lo[CH];
 #pragma unroll
-            for (int i = 0; i < NQ / 4; ++i) {
-                const int j = r0 + 4 * i;
-                qid[i] = j < nq ? A.qlist[q0pos + j] / A.S : -1;
+            for (int q = 0; q < CH; ++q) {
+                t[q] = rows[q] = q0pos[q] = nq[q] = 0;
+                lo[q] = 0;
+                if (item_lo + wu * CH + q < item_hi) chunk_of(F, A, item_lo + wu * CH + q, t[q], lo[q], rows[q], q0pos[q], nq[q]);
             }
-            const int nst = (rows + BM - 1) / BM * KC * SUB;  // the chunk's sub-tiles
+            // B row j = r0 + 4 i: query j % NQ of chunk j / NQ (= i / 4, as r0 < 4)
+            int qid[NQT / 4];
+#pragma unroll
+            for (int i = 0; i < NQT / 4; ++i) {
+                const int q = i / 4, j = r0 + 4 * (i % 4);
+                qid[i] = j < nq[q] ? A.qlist[q0pos[q] + j] / A.S : -1;
+            }
+            const int nst = (CH == 1 ? (rows[0] + BM - 1) / BM : 1) * KC * SUB;  // the unit's sub-tiles
             int ids[BM / 4];  // point ids of the lane's rows of tile `cur`
             int cur = -1;
             for (int sh = (int)((pw + PROD_WARPS - it % PROD_WARPS) % PROD_WARPS); sh < nst; sh += PROD_WARPS) {
@@ -445,10 +466,12 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
                 const int mt = st / KC, kc = st - mt * KC;
                 if (mt != cur) {
                     cur = mt;
+                    // tile row r0 + 4 i: row r0 + 4 (i % (ROWS_PER / 4)) of chunk i / (ROWS_PER / 4)
 #pragma unroll
                     for (int i = 0; i < BM / 4; ++i) {
-                        const int gr = mt * BM + r0 + 4 * i;
-                        ids[i] = gr < rows ? __ldg(F.perm + (size_t)t * F.n + lo + gr) : -1;
+                        const int q = i / (ROWS_PER / 4);
+                        const int gr = mt * BM + r0 + 4 * (i % (ROWS_PER / 4));
+                        ids[i] = gr < rows[q] ? __ldg(F.perm + (size_t)t[q] * F.n + lo[q] + gr) : -1;
                     }
                 }
                 if (!mbar_wait(empty + s, ((g / STAGES) & 1) ^ 1, abort_flag, A.wait_ns)) { ok = false; break; }
@@ -467,14 +490,14 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
                     const unsigned char *src = live ? xrows + (size_t)ids[i] * pitch + col : xrows;
                     cp_async16(sa + r * 128 + ((c ^ (r & 7)) << 4), src, live ? nb : 0);
                 }
-                if (held_w != w || held_k != kbyte) {
-                    held_w = w;
+                if (held_w != wu || held_k != kbyte) {
+                    held_w = wu;
                     held_k = kbyte;
 #pragma unroll
                     for (int h = 0; h < QP; ++h) {
                         const unsigned char *qb = A.qpart + h * A.qpart_stride;
 #pragma unroll
-                        for (int i = 0; i < NQ / 4; ++i) {
+                        for (int i = 0; i < NQT / 4; ++i) {
                             const int j = r0 + 4 * i;
                             const bool live = qid[i] >= 0 && nb > 0;
                             const unsigned char *src = live ? qb + (size_t)qid[i] * pitch + col : qb;
@@ -497,11 +520,14 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
             bool ok = true;
             const uint64_t da0 = sdesc_sw128(stage0);            // stage 0's leaf rows
             const uint64_t db0 = sdesc_sw128(stage0 + A_BYTES);  // stage 0's query parts
-            for (int w = item_lo + blockIdx.x; w < item_hi && ok; w += gridDim.x) {
-                int t, rows, q0pos, nq;
-                long long lo;
-                chunk_of(F, A, w, t, lo, rows, q0pos, nq);
-                const int MT = (rows + BM - 1) / BM;
+            for (int wu = blockIdx.x; item_lo + wu * CH < item_hi && ok; wu += gridDim.x) {
+                int MT = 1;  // two chunks a tile: leaves of at most 64 rows, one tile
+                if (CH == 1) {
+                    int t, rows, q0pos, nq;
+                    long long lo;
+                    chunk_of(F, A, item_lo + wu, t, lo, rows, q0pos, nq);
+                    MT = (rows + BM - 1) / BM;
+                }
                 for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
                     const uint32_t buf = tile & 1;
                     if (!mbar_wait(dempty + buf, ((tile >> 1) & 1) ^ 1, abort_flag, A.wait_ns)) { ok = false; break; }
@@ -514,7 +540,7 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
                             const int kbyte = (kc * SUB + u) * 128;
                             if (kbyte >= row_bytes) break;
                             const uint64_t off = (uint64_t)((s * STAGE_BYTES + u * SUBTILE_BYTES) >> 4);
-                            mma_slice<FMT>(d_tmem, da0 + off, db0 + off, (kc | u) != 0, (row_bytes - kbyte + 31) >> 5);
+                            mma_slice<FMT, CH>(d_tmem, da0 + off, db0 + off, (kc | u) != 0, (row_bytes - kbyte + 31) >> 5);
                         }
                         mma_commit(empty + s);
                         if (++s == STAGES) { s = 0; ph ^= 1; }
@@ -532,12 +558,13 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue: screened keys, R best per query
-        // Each warp keeps, for every query of the chunk, the list of the R best keys of its own
+        // Each warp keeps, for every query of its chunk, the list of the R best keys of its own
         // 32 rows of every tile (in shared memory, with the list's bound: its R-th key or tau_q);
-        // the four lists are merged when the chunk is done.  A tile's scores go through shared
-        // memory too, so that the query loop is a short rolled loop (four queries a turn) and not
-        // one unrolled copy per query.
+        // the chunk's LW lists are merged when the chunk is done.  A tile's scores go through
+        // shared memory too, so that the query loop is a short rolled loop (four queries a turn)
+        // and not one unrolled copy per query.
         const int et = tid;  // tile row and tensor-memory lane
+        const int cw = warp / LW, wi = warp % LW;  // the chunk of the warp's rows; the warp's rank in it
         const int R = A.R;
         int RL = 1;
         while (RL < R) RL <<= 1;
@@ -546,10 +573,10 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
         unsigned long long *sthr = reinterpret_cast<unsigned long long *>(sm + Cfg::SM_THR) + warp * NQ;
         uint32_t tile = 0;
         bool ok = true;
-        for (int w = item_lo + blockIdx.x; w < item_hi; w += gridDim.x) {
-            int t, rows, q0pos, nq;
-            long long lo;
-            chunk_of(F, A, w, t, lo, rows, q0pos, nq);
+        for (int wu = blockIdx.x; item_lo + wu * CH < item_hi; wu += gridDim.x) {
+            int t = 0, rows = 0, q0pos = 0, nq = 0;  // an absent second chunk: no rows, no queries
+            long long lo = 0;
+            if (item_lo + wu * CH + cw < item_hi) chunk_of(F, A, item_lo + wu * CH + cw, t, lo, rows, q0pos, nq);
             // lane j: query j of the chunk, its bound and (E4M3 parts) the scale of its part 0
             const int my_qid = lane < nq ? A.qlist[q0pos + lane] / A.S : 0;
             const unsigned long long my_tau = lane < nq ? __ldcg(A.tau + my_qid) : KEY_NONE;
@@ -557,9 +584,9 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
             for (int j = 0; j < nq; ++j) sl[j * 32 + lane] = KEY_NONE;
             if (lane < nq) sthr[lane] = my_tau;
             __syncwarp();
-            const int MT = (rows + BM - 1) / BM;
+            const int MT = CH == 1 ? (rows + BM - 1) / BM : 1;  // the MMA's tiles of this unit
             for (int mt = 0; mt < MT && ok; ++mt, ++tile) {
-                const int r = mt * BM + et;
+                const int r = mt * BM + et - cw * ROWS_PER;  // the lane's row of its chunk's leaf
                 const bool valid = r < rows;
                 const int id = valid ? __ldg(F.perm + (size_t)t * F.n + lo + r) : 0;
                 // |x~|^2 and the factor of x~.q in the score: -2 (bf16), -2 s_x (E4M3 codes)
@@ -574,7 +601,7 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
                 {
                     uint32_t acc[QP][16];
 #pragma unroll
-                    for (int p = 0; p < QP; ++p) tmem_ld16(ta + p * NQ, acc[p]);
+                    for (int p = 0; p < QP; ++p) tmem_ld16(ta + p * NQT + cw * NQ, acc[p]);
                     tmem_wait();
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
@@ -619,19 +646,23 @@ __global__ void __maxnreg__((LeafCfg<FMT, CPS>::REGS)) k_leaf_score(ForestView F
                     }
                 }
             }
-            // all four warps are done with the chunk's lists
+            // all four warps are done with the unit's lists; the warps of each chunk merge its LW
             if (epi_any(!ok)) break;
-            for (int j = warp; j < nq; j += 4) {
-                unsigned long long a = wl[(0 * NQ + j) * 32 + lane], b = wl[(1 * NQ + j) * 32 + lane];
-                unsigned long long c = wl[(2 * NQ + j) * 32 + lane], d = wl[(3 * NQ + j) * 32 + lane];
+            for (int j = wi; j < nq; j += LW) {
+                const unsigned long long *lw0 = wl + (size_t)(cw * LW) * NQ * 32;  // the chunk's first list
+                unsigned long long a = lw0[(0 * NQ + j) * 32 + lane], b = lw0[(1 * NQ + j) * 32 + lane];
+                unsigned long long c = LW == 4 ? lw0[(2 * NQ + j) * 32 + lane] : KEY_NONE;
+                unsigned long long d = LW == 4 ? lw0[(3 * NQ + j) * 32 + lane] : KEY_NONE;
                 if (lane >= RL) a = b = c = d = KEY_NONE;
-                const unsigned long long best = warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL);
+                const unsigned long long best =
+                    LW == 4 ? warp_merge_top(warp_merge_top(a, b, RL), warp_merge_top(c, d, RL), RL)
+                            : warp_merge_top(a, b, RL);
                 const int pr = A.qlist[q0pos + j];
                 if (lane < R) A.part[(size_t)pr * R + lane] = best;
                 const unsigned long long kth = __shfl_sync(FULL, best, R - 1);
                 if (lane == 0 && kth != KEY_NONE) atomicMin(A.tau + pr / A.S, kth);
             }
-            epi_sync();  // the merges have read the lists before the next chunk resets them
+            epi_sync();  // the merges have read the lists before the next unit resets them
         }
     }
     tc_fence_before();
@@ -1070,16 +1101,29 @@ LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int S, int R, int or
 
 int order_of(int order) { return order == GF_ORDER_GIVEN ? GF_ORDER_GIVEN : GF_ORDER_LOCALITY; }
 
-template <int FMT, int CPS>
+template <int FMT, int CPS, int CH>
 cudaError_t leaf_smem_attr() {
-    return cudaFuncSetAttribute(k_leaf_score<FMT, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                LeafCfg<FMT, CPS>::SMEM_BYTES);
+    return cudaFuncSetAttribute(k_leaf_score<FMT, CPS, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                LeafCfg<FMT, CPS, CH>::SMEM_BYTES);
 }
 
-template <int FMT, int CPS>
+template <int FMT, int CPS, int CH>
 void launch_score(const gf_forest *F, const LeafArgs &A, cudaStream_t st) {
-    using Cfg = LeafCfg<FMT, CPS>;
-    k_leaf_score<FMT, CPS><<<F->num_sms * Cfg::CTAS_PER_SM, Cfg::THREADS, Cfg::SMEM_BYTES, st>>>(view_of(F), A);
+    using Cfg = LeafCfg<FMT, CPS, CH>;
+    k_leaf_score<FMT, CPS, CH><<<F->num_sms * Cfg::CTAS_PER_SM, Cfg::THREADS, Cfg::SMEM_BYTES, st>>>(view_of(F), A);
+}
+
+// the tensor-core kernel for a format, shape (CTAs per SM) and chunks per tile
+template <int FMT>
+cudaError_t score_attr(int cps, int ch) {
+    return cps == 1 ? (ch == 2 ? leaf_smem_attr<FMT, 1, 2>() : leaf_smem_attr<FMT, 1, 1>())
+                    : (ch == 2 ? leaf_smem_attr<FMT, 2, 2>() : leaf_smem_attr<FMT, 2, 1>());
+}
+
+template <int FMT>
+void score_launch(int cps, int ch, const gf_forest *F, const LeafArgs &A, cudaStream_t st) {
+    if (cps == 1) ch == 2 ? launch_score<FMT, 1, 2>(F, A, st) : launch_score<FMT, 1, 1>(F, A, st);
+    else ch == 2 ? launch_score<FMT, 2, 2>(F, A, st) : launch_score<FMT, 2, 1>(F, A, st);
 }
 
 }  // namespace
@@ -1108,12 +1152,17 @@ const char *gf_leaf_unsupported(const gf_forest *F, int64_t m, int32_t k, int32_
 // The regrouping pays once leaves are shared: on average at least LEAF_MIN_SHARE queries per leaf.
 constexpr int LEAF_MIN_SHARE = 4;
 
-// The priority search is left to the streaming kernel: its leaves are small (the paper's p of a
-// few dozen points), a chunk fills part of a row tile, and per-chunk costs dominate (at 10^6 x 960,
-// p = 64, c = 512: 57.7 ms against 45.6 ms per 10^4 queries, bf16).  GF_ALGO_LEAF still runs it.
+// Sharing is m S / (T 2^L) queries per (tree, leaf): m / 2^L for one leaf per tree, and for the
+// priority search with S leaves a query as many as its budget spreads over the forest's leaves.
+// The priority search's small leaves (the paper's p of a few dozen points) pair up in the
+// tensor-core kernel's row tiles (at 10^6 x 960, p = 64, c = 512: 37.3 ms against 45.7 ms for the
+// streaming kernel per 10^4 queries, bf16); the float32 kernel's 256-row tiles would stay mostly
+// empty there, so float32 priority searches remain with the streaming kernel.
 bool gf_leaf_preferred(const gf_forest *F, int64_t m, int32_t k, int32_t precision, int32_t R, const QueryExtra &x) {
-    return x.leaf_budget == 0 && gf_leaf_unsupported(F, m, k, precision, R, x) == nullptr &&
-           (m >> F->L) >= LEAF_MIN_SHARE;
+    if (x.leaf_budget > 0 && precision == GF_FP32) return false;
+    const int64_t S = x.leaf_budget > 0 ? x.leaf_budget : F->T;
+    return gf_leaf_unsupported(F, m, k, precision, R, x) == nullptr &&
+           m * S / ((int64_t)F->T << F->L) >= LEAF_MIN_SHARE;
 }
 
 int64_t gf_leaf_workspace_bytes(const gf_forest *F, int64_t m, int32_t precision, int32_t R, int32_t order,
@@ -1199,9 +1248,10 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     // the tensor-core kernel's shape: one CTA per SM when the caller or the forest's tuning asks for
     // exactly one, else two
     const int cps = ctas_per_sm == 1 ? 1 : 2;
+    // two chunks share a row tile when no leaf has more than 64 rows (half a tile)
+    const int ch = ((F->n + (1ll << F->L) - 1) >> F->L) <= BM / 2 ? 2 : 1;
     e = f32 ? cudaFuncSetAttribute(k_leaf_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, f32k::SMEM)
-        : f8 ? (cps == 1 ? leaf_smem_attr<LF_FP8, 1>() : leaf_smem_attr<LF_FP8, 2>())
-             : (cps == 1 ? leaf_smem_attr<LF_BF16, 1>() : leaf_smem_attr<LF_BF16, 2>());
+        : f8 ? score_attr<LF_FP8>(cps, ch) : score_attr<LF_BF16>(cps, ch);
     if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute(leaf-major scoring)");
     LeafArgs A;
     A.items = items;
@@ -1224,8 +1274,8 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
         A.item_lo = wave == 0 ? koff : koff + (1 << F->L);
         A.item_hi = wave == 0 ? koff + (1 << F->L) : koff + nk;
         if (f32) k_leaf_f32<<<F->num_sms * f32k::CTAS_PER_SM, f32k::THREADS, f32k::SMEM, st>>>(view_of(F), A);
-        else if (f8) cps == 1 ? launch_score<LF_FP8, 1>(F, A, st) : launch_score<LF_FP8, 2>(F, A, st);
-        else cps == 1 ? launch_score<LF_BF16, 1>(F, A, st) : launch_score<LF_BF16, 2>(F, A, st);
+        else if (f8) score_launch<LF_FP8>(cps, ch, F, A, st);
+        else score_launch<LF_BF16>(cps, ch, F, A, st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "leaf-major scoring launch");
     if (events && (e = cudaEventRecord(events[1], st)) != cudaSuccess) return fail(e, "cudaEventRecord");
