@@ -909,7 +909,61 @@ __global__ void k_item_fill(int nb, const int *__restrict__ bcnt, const int *__r
     for (int i = 0; i < n_it; ++i) items[base + i] = make_int2(u, i * NQ);
 }
 
-// Exclusive prefix sum of a[0..N) into off[0..N], off[N] = total; one CTA of 1024 threads.
+constexpr int SCAN_TILE = 4096;  // elements one CTA of k_scan_tiles scans (four a thread)
+
+// Exclusive prefix sums within the tiles of a[0..N): off[i] = the sum of a over [i's tile start,
+// i), tsum[b] = tile b's total.  Thread t takes four consecutive elements (coalesced loads); the
+// thread sums are scanned by warp shuffles, then the 32 warp totals by warp 0.
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int *__restrict__ a, int N, int *off, int *tsum) {
+    __shared__ int wsum[32];
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int v[4], s = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        v[e] = base + e < N ? a[base + e] : 0;
+        s += v[e];
+    }
+    int inc = s;  // inclusive scan of the warp's thread sums
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int x = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        wsum[lane] = x;  // inclusive over the warps
+    }
+    __syncthreads();
+    int run = inc - s + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (base + e < N) off[base + e] = run;
+        run += v[e];
+    }
+    if (threadIdx.x == 1023) tsum[blockIdx.x] = wsum[31];
+}
+
+// Adds each tile's offset toff[b] (the exclusive scan of the tile totals) to its elements, and
+// writes off[N] = the total.
+__global__ void __launch_bounds__(1024) k_scan_add(int N, int *off, const int *__restrict__ toff) {
+    const int i = blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    const int add = toff[blockIdx.x];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (i + e < N) off[i + e] += add;
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[N] = toff[gridDim.x];
+}
+
+// Exclusive prefix sum of a[0..N) into off[0..N], off[N] = total; one CTA of 1024 threads (the
+// tile totals of k_scan_tiles).
 __global__ void __launch_bounds__(1024) k_scan(const int *__restrict__ a, int N, int *off) {
     __shared__ int part[1024];
     const int per = (N + 1023) / 1024;
@@ -1004,10 +1058,12 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
     int Pmax = 2;
     while (Pmax < TR) Pmax <<= 1;
     unsigned long long *a = reinterpret_cast<unsigned long long *>(smem_raw);
-    unsigned long long *b = a + Pmax;
-    float *qs = reinterpret_cast<float *>(b + Pmax);
+    float *qs = reinterpret_cast<float *>(a + Pmax);
     int *sid = reinterpret_cast<int *>(qs + ldq_of(F.d));
+    unsigned char *dup = reinterpret_cast<unsigned char *>(sid + R);  // [Pmax]
     __shared__ int nshort, nkeep;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     for (long long qi = blockIdx.x; qi < m; qi += gridDim.x) {
         const unsigned long long tq = tau[qi];
         if (threadIdx.x == 0) {
@@ -1016,12 +1072,29 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
         }
         __syncthreads();
         // the keys that can still be among the R best, as (id, score): the copies of an id
-        // come together, its best score first
-        for (int i = threadIdx.x; i < TR; i += blockDim.x) {
-            const unsigned long long key = part[qi * TR + i];
-            // (an id outside [0, n) is a list no scoring CTA wrote: its launch gave up a wait)
-            if (key != KEY_NONE && key <= tq && (key & 0xffffffffull) < (unsigned long long)F.n)
-                a[atomicAdd(&nkeep, 1)] = (key << 32) | (key >> 32);
+        // come together, its best score first.  Eight loads in flight a thread; a warp appends its
+        // keepers with one atomic.
+        const unsigned long long *pq = part + qi * TR;
+        for (int base = 0; base < TR; base += blockDim.x * 8) {
+            unsigned long long kv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = base + u * blockDim.x + threadIdx.x;
+                kv[u] = i < TR ? __ldcs(pq + i) : KEY_NONE;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const unsigned long long key = kv[u];
+                // (an id outside [0, n) is a list no scoring CTA wrote: its launch gave up a wait)
+                const bool keep = key != KEY_NONE && key <= tq && (key & 0xffffffffull) < (unsigned long long)F.n;
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (bal) {
+                    int at = 0;
+                    if (lane == 0) at = atomicAdd(&nkeep, __popc(bal));
+                    at = __shfl_sync(FULL, at, 0);
+                    if (keep) a[at + __popc(bal & lt)] = (key << 32) | (key >> 32);
+                }
+            }
         }
         __syncthreads();
         const int n = nkeep;
@@ -1029,15 +1102,17 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
         while (P < n) P <<= 1;
         for (int i = n + threadIdx.x; i < P; i += blockDim.x) a[i] = KEY_NONE;
         block_sort<unsigned long long>(a, P);
+        // every id once, with its best score; back to (score, id) for the second sort
+        for (int i = threadIdx.x; i < P; i += blockDim.x) dup[i] = i > 0 && (a[i] >> 32) == (a[i - 1] >> 32);
+        __syncthreads();
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const unsigned long long v = a[i];
-            const bool dup = i > 0 && (v >> 32) == (a[i - 1] >> 32);
-            b[i] = dup ? KEY_NONE : ((v << 32) | (v >> 32));
+            a[i] = dup[i] ? KEY_NONE : ((v << 32) | (v >> 32));
         }
-        block_sort<unsigned long long>(b, P);
+        block_sort<unsigned long long>(a, P);
         for (int i = threadIdx.x; i < R && i < P; i += blockDim.x) {
-            if (b[i] != KEY_NONE) {
-                sid[i] = (int)(unsigned)(b[i] & 0xffffffffu);
+            if (a[i] != KEY_NONE) {
+                sid[i] = (int)(unsigned)(a[i] & 0xffffffffu);
                 atomicAdd(&nshort, 1);
             }
         }
@@ -1045,11 +1120,12 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
         __syncthreads();
         const int C = nshort;  // the valid keys are a prefix of the sorted list
         if (rerank) {
+            // the shortlist's ids are in sid: the keys' buffer is free for the float32 scores
             rescore_f32<NCF>(F, qs, sid, C, a);
             sort_keys(a, C);
             write_topk(a, C, k, ids + qi * k, dists + qi * k);
         } else {  // the keys are float32 distances already, in order
-            write_topk(b, C, k, ids + qi * k, dists + qi * k);
+            write_topk(a, C, k, ids + qi * k, dists + qi * k);
         }
         __syncthreads();
     }
@@ -1058,14 +1134,14 @@ __global__ void __launch_bounds__(128) k_leaf_merge(ForestView F, const float *_
 size_t merge_smem(const gf_forest *F, int S, int R) {
     int P = 2;
     while (P < S * R) P <<= 1;
-    return (size_t)2 * P * 8 + (size_t)ldq_of(F->d) * 4 + (size_t)R * 4;
+    return (size_t)P * 8 + (size_t)ldq_of(F->d) * 4 + (size_t)R * 4 + (size_t)P;
 }
 
 // ---------------------------------------------------------------- workspace
 
 struct LeafWorkspace {
     size_t bcnt, bfill, kcnt, kfill, zero_end;  // counters, zeroed by every call
-    size_t boff, koff, leaf, pn, qlist, items, qpart, qc, part, tau, total;
+    size_t boff, koff, tsum, toff, leaf, pn, qlist, items, qpart, qc, part, tau, total;
     size_t qpart_stride;  // bytes per query part ([m] rows)
 };
 
@@ -1084,6 +1160,9 @@ LeafWorkspace leaf_workspace(const gf_forest *F, int64_t m, int S, int R, int or
     W.zero_end = o;
     W.boff = o; o = al(o + (nb + 1) * 4);
     W.koff = o; o = al(o + (nk + 1) * 4);
+    const size_t nt = (std::max(nb, nk) + SCAN_TILE - 1) / SCAN_TILE;  // scan tiles
+    W.tsum = o; o = al(o + nt * 4);
+    W.toff = o; o = al(o + (nt + 1) * 4);
     W.leaf = o; o = al(o + pairs * 4);  // leaf[m][T] or the priority lists [m][S]
     W.pn = o; o = al(o + (size_t)m * 4);
     W.qlist = o; o = al(o + pairs * 4);
@@ -1229,11 +1308,18 @@ int gf_launch_leaf(const gf_forest *F, const float *Q, int64_t m, int32_t k, int
     P.S = S;
     P.L = F->L;
     const unsigned pg = (unsigned)((pairs + 255) / 256), bg = (unsigned)((nb + 255) / 256);
+    int *tsum = (int *)(ws + W.tsum), *toff = (int *)(ws + W.toff);
+    auto scan = [&](const int *a, int N, int *off) {  // exclusive scan: tiles, their totals, the offsets
+        const int nt = (N + SCAN_TILE - 1) / SCAN_TILE;
+        k_scan_tiles<<<nt, 1024, 0, st>>>(a, N, off, tsum);
+        k_scan<<<1, 1024, 0, st>>>(tsum, nt, toff);
+        k_scan_add<<<nt, 1024, 0, st>>>(N, off, toff);
+    };
     k_pair_count<<<pg, 256, 0, st>>>(pairs, P, bcnt);
-    k_scan<<<1, 1024, 0, st>>>(bcnt, nb, boff);
+    scan(bcnt, nb, boff);
     k_pair_fill<<<pg, 256, 0, st>>>(pairs, P, boff, bfill, qlist);
     k_item_count<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, P, locality, kcnt);
-    k_scan<<<1, 1024, 0, st>>>(kcnt, nk, koff);
+    scan(kcnt, nk, koff);
     k_item_fill<<<bg, 256, 0, st>>>(nb, bcnt, boff, qlist, P, locality, koff, kfill, items);
     // the queries as the scoring kernel reads them: the float32 kernel's padded copy, the bf16 parts
     // hi and lo, or the three E4M3 parts and their scales
