@@ -103,6 +103,29 @@ def test_leaf_one_cta_shape_matches_oracle(gf, name, prec):
     assert gf.gf_kernel_status() == 0
 
 
+@pytest.mark.parametrize("m", [1001, 3000])
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_leaf_paired_chunks_at_the_limit(gf, m, prec):
+    # leaves of exactly 64 rows (4096 points, 2^6 leaves): two chunks share every row tile; 1001
+    # queries give buckets of one or two chunks (a wave may end on an unpaired chunk), 3000 give
+    # three or more (two chunks of one leaf share a tile); both shapes, against the oracle
+    X, Q = synth.mixture(4096, 96, m, "B", seed=5, qseed=6)
+    F = oracle.build_forest(X, 5, 64, t=5, seed=3)
+    assert F.L == 6 and (F.n >> F.L) == 64
+    G = gpu_forest(gf, X, F)
+    k, R = 10, 16
+    Qg = torch.from_numpy(Q).cuda()
+    p = gf.PRECISIONS[prec]
+    oi, od, cands = oracle_screen(F, X, Q, k, R, prec)
+    res = []
+    for cps in (0, 1):
+        gi, gd = gf.gf_query(G, Qg, k, precision=p, rerank_R=R, algo=gf.GF_ALGO_LEAF, ctas_per_sm=cps)
+        assert_screened_close(X, Q, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, *cands, prec, R, "norm")
+        res.append((gi, gd))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    assert gf.gf_kernel_status() == 0
+
+
 @pytest.mark.parametrize("k,R", [(1, 1), (1, 16), (5, 16), (7, 7)])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_leaf_small_k(gf, k, R, prec):
