@@ -11,10 +11,14 @@
 // value does: the queue compares the bits as 64-bit integers (GB300's float64 compare rate is a
 // small fraction of its integer rate).
 //
-// One warp per query.  The queue is a sorted array in shared memory; the entries a descent pushes
-// (at most L <= 30, or one per tree in the first phase) are merged into it by the warp.  Entries
-// ranked beyond the number of pops still to come can never be taken and are dropped, so the array
-// never holds more than `budget` + 32 entries.  The output is the list of leaves in the order
+// One warp per query.  The queue is two sorted arrays in shared memory: a large one A and a small
+// one B (at most 64 entries).  A pop takes the smaller of their heads.  The entries a descent pushes
+// (at most L <= 30) are merged into B by the warp; once B holds more than 32 it is merged into A in
+// place (from the top down), so the large array moves once every few pops instead of at every one.
+// The first phase (one entry per tree and level) merges into A directly.  Entries ranked beyond the
+// number of pops still to come can never be taken and are dropped, so A never holds more than
+// `budget` entries past its head.  The order of the pops is that of a single sorted queue: every
+// pop takes the smallest (key, tree, node) held.  The output is the list of leaves in the order
 // checked, encoded (tree << L) | leaf.
 #include "gf_internal.cuh"
 #include "gf_trace.cuh"
@@ -88,14 +92,74 @@ __device__ int pq_merge(const PQE *src, int cnt, PQE *stage, int nb, PQE *dst, i
     return min(cnt + nb, keep);
 }
 
+// Number of entries of the sorted array a[0..n) below e.  Warp lanes call it independently.
+__device__ __forceinline__ int pq_lower(const PQE *a, int n, const PQE &e) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pq_less(a[mid], e)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// sorted[0..nb) = the nb (<= 32) staged entries in order.  Warp-wide.
+__device__ void pq_sort_stage(const PQE *stage, int nb, PQE *sorted) {
+    const int lane = threadIdx.x & 31;
+    const PQE mine = lane < nb ? stage[lane] : pq_inf();
+    int r = 0;
+    for (int i = 0; i < nb; ++i) r += pq_less(stage[i], mine);
+    __syncwarp();
+    if (lane < nb) sorted[r] = mine;
+    __syncwarp();
+}
+
+// Merge the sorted array s[0..ns) (ns <= 64, not overlapping a) into the sorted array a[0..na) in
+// place, keeping the first min(na + ns, keep) entries of the merged order in a[]; returns their
+// number.  a[] must have room for them.  An entry of a moves up by the number of s entries below
+// it, so a is moved from the top down, 32 entries at a time, each group read before it is written.
+// Warp-wide.
+__device__ int pq_merge_into(PQE *a, int na, const PQE *s, int ns, int keep) {
+    const int lane = threadIdx.x & 31;
+    // the positions of s's entries in the merged order, against a as it is now
+    int ps[2];
+    PQE es[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        es[h] = i < ns ? s[i] : pq_inf();
+        ps[h] = i < ns ? i + pq_lower(a, na, es[h]) : keep;
+    }
+    __syncwarp();
+    for (int top = na; top > 0; top -= 32) {
+        const int j = top - 32 + lane;
+        PQE e;
+        int pos = keep;
+        if (j >= 0) {
+            e = a[j];
+            pos = j + pq_lower(s, ns, e);
+        }
+        __syncwarp();
+        if (j >= 0 && pos < keep) a[pos] = e;
+        __syncwarp();
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (ps[h] < keep) a[ps[h]] = es[h];
+    __syncwarp();
+    return min(na + ns, keep);
+}
+
 __device__ __forceinline__ unsigned leaf_code(int tree, int leaf, int L) {
     return ((unsigned)tree << L) | (unsigned)leaf;
 }
 
-// per-warp shared memory: two queue arrays of `cap` entries, the staged batch and its sorted copy,
-// then one reflection weight per tree
+constexpr int PQ_BCAP = 64;  // entries of each small queue array
+
+// per-warp shared memory: the large queue array (`budget` + 64 entries), the small one (two
+// buffers), the staged batch and its sorted copy, then one reflection weight per tree
 __host__ __device__ inline size_t prio_warp_bytes(int budget, int T) {
-    return (size_t)(2 * (budget + 32) + 64) * sizeof(PQE) + (size_t)(T + 3) / 4 * 16;
+    return (size_t)(budget + 64 + 2 * PQ_BCAP + 64) * sizeof(PQE) + (size_t)(T + 3) / 4 * 16;
 }
 
 __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, const float *__restrict__ Q,
@@ -105,14 +169,16 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned char *mine = smem_raw + (size_t)w * prio_warp_bytes(budget, F.T);
     PQE *base = reinterpret_cast<PQE *>(mine);
-    PQE *qa = base, *qb = base + cap, *stage = base + 2 * cap, *sorted = stage + 32;
-    float *w2s = reinterpret_cast<float *>(base + 2 * cap + 64);
+    PQE *qa = base;                                   // A [cap]
+    PQE *qb = base + cap, *qb2 = qb + PQ_BCAP;        // B, double-buffered
+    PQE *stage = qb2 + PQ_BCAP, *sorted = stage + 32;
+    float *w2s = reinterpret_cast<float *>(sorted + 32);
     const int nn = (1 << F.L) - 1;
     const int nwq = blockDim.x >> 5;
     for (long long qi = (long long)blockIdx.x * nwq + w; qi < m; qi += (long long)gridDim.x * nwq) {
         const float *q = Q + qi * F.d;
         unsigned *out = leaves + qi * budget;
-        int cnt = 0, head = 0, checked = 0;
+        int acnt = 0, ahead = 0, bcnt = 0, bhead = 0, checked = 0;  // A holds [ahead, acnt), B [bhead, bcnt)
         // ---- first descent of every tree, 32 trees at a time, one level per merge
         for (int t0 = 0; t0 < F.T; t0 += 32) {
             const int t = t0 + lane;
@@ -139,17 +205,20 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
                 __syncwarp();
                 const int nb = min(32, F.T - t0);
                 const int keep = min(cap, max(0, budget - F.T));
-                cnt = pq_merge(qa, cnt, stage, nb, qb, keep, sorted);
-                PQE *tmp = qa; qa = qb; qb = tmp;
-                __syncwarp();
+                pq_sort_stage(stage, nb, sorted);
+                acnt = pq_merge_into(qa, acnt, sorted, nb, keep);
             }
             if (act && t < budget) out[t] = leaf_code(t, j - nn, F.L);
         }
         checked = min(F.T, budget);
         // ---- pops in queue order
-        while (checked < budget && head < cnt) {
-            const PQE top = qa[head];
-            ++head;
+        while (checked < budget && (ahead < acnt || bhead < bcnt)) {
+            // the smaller head of A and B
+            const PQE ta = ahead < acnt ? qa[ahead] : pq_inf(), tb = bhead < bcnt ? qb[bhead] : pq_inf();
+            const bool fromb = pq_less(tb, ta);
+            const PQE top = fromb ? tb : ta;
+            if (fromb) ++bhead;
+            else ++ahead;
             // descend from the popped node, staging the siblings passed.  The warp loads the
             // five-level subtree below the current node at once (lane i: node i in breadth-first
             // order, with its query coordinate), then walks it through shuffles: five levels cost
@@ -189,12 +258,16 @@ __global__ void __launch_bounds__(PRIO_WARPS * 32) k_prio_leaves(ForestView F, c
             if (lane == 0) out[checked] = leaf_code(tr, j - nn, F.L);
             __syncwarp();
             ++checked;
-            // drop the popped prefix while merging; keep only what later pops can still take
-            const int keep = min(cap, max(0, budget - checked));
-            cnt = pq_merge(qa + head, cnt - head, stage, nb, qb, keep, sorted);
-            head = 0;
-            PQE *tmp = qa; qa = qb; qb = tmp;
+            // the pushes go to B (its popped prefix dropped); keep only what later pops can take
+            const int keep = max(0, budget - checked);
+            bcnt = pq_merge(qb + bhead, bcnt - bhead, stage, nb, qb2, min(PQ_BCAP, keep), sorted);
+            bhead = 0;
+            PQE *tmp = qb; qb = qb2; qb2 = tmp;
             __syncwarp();
+            if (bcnt > PQ_BCAP - 32) {  // the next pushes might not fit: B into A
+                acnt = ahead + pq_merge_into(qa + ahead, acnt - ahead, qb, bcnt, keep);
+                bcnt = 0;
+            }
         }
         if (lane == 0) nleaves[qi] = checked;
         __syncwarp();
@@ -207,7 +280,7 @@ size_t gf_prio_smem_bytes(int budget, int T) { return prio_warp_bytes(budget, T)
 
 int gf_launch_prio_leaves(const gf_forest *F, const float *Q, int64_t m, int budget, unsigned *leaves,
                           int *nleaves, cudaStream_t st) {
-    const int cap = budget + 32;
+    const int cap = budget + 64;
     int dev = 0, lim = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

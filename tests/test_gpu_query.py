@@ -324,8 +324,9 @@ def test_locality_order_changes_no_result(gf, prec):
 # ---------------------------------------------------------------- Alg. 2 priority search
 
 @pytest.mark.parametrize("name,c", [("tiny", 24), ("ragged", 23), ("manytrees", 100), ("gist_like", 64),
-                                    ("klein", 32)])
+                                    ("klein", 32), ("gist_like", 512), ("manytrees", 300)])
 def test_priority_leaf_order_bit_exact(gf, name, c):
+    # (budgets of hundreds of leaves move the queue's small array into its large one many times)
     X, Q, F = case(name)
     G, _ = gpu_forest(gf, X, F)
     leaves, nl = gf.gf_prio_leaves(G, torch.from_numpy(Q).cuda(), c)
